@@ -1,0 +1,165 @@
+"""Krylov solvers for the complex FE Helmholtz system (oracle; test infrastructure).
+
+Paper Sec. 4 solves the complex double-precision acoustic system with Krylov methods
+(after Saad, "Iterative Methods for Sparse Linear Systems"). The oracle states, step
+by step in complex128 numpy, the two iterations the GPU path runs:
+
+* ``gmres``: restarted GMRES(m), x0 = 0, right preconditioning x = M^-1 u, Arnoldi with
+  classical Gram-Schmidt applied twice ("cgs2", default) or modified Gram-Schmidt
+  ("mgs"), complex Givens rotations on the Hessenberg matrix (Saad 2nd ed. Sec. 6.5),
+  residual estimate |g_{j+1}| checked every step; at the end of a cycle x += M^-1 V y and
+  the true residual ||b - A x|| decides convergence or restart.
+  Givens reading: a = h_jj, b = h_{j+1,j} (real >= 0), r = sqrt(|a|^2 + b^2),
+  c = |a|/r, s = (a/|a|) b/r; c = 0, s = 1 when a = 0. Rotation (x, y) ->
+  (c x + s y, -conj(s) x + c y).
+* ``cocg``: conjugate orthogonal CG (van der Vorst & Melissen 1990) for complex-symmetric
+  A: CG with the unconjugated bilinear form x^T y. Stop when ||r_rec||/||b|| <= tol, then
+  the true residual is checked; if it misses tol the iteration restarts from the current
+  x with r = b - A x.
+
+Iteration count = number of Krylov steps (products with A inside the iteration; the
+true-residual products are not counted).
+
+Pinned (tests/test_oracle_krylov.py): solutions equal dense LU (numpy.linalg.solve) on
+small meshes, the discrete duct / rigid-box forced-mode solutions are reproduced to
+round-off, a 1x1x1 Schwarz partition converges in one step, Givens rotations annihilate
+and are unitary. Iteration counts themselves are parity-unpinned (the paper prints none
+for these methods).
+"""
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Stats:
+    iterations: int = 0
+    restarts: int = 0
+    converged: bool = False
+    relres: float = np.inf         # true ||b - A x|| / ||b|| at exit
+    breakdown: bool = False
+    history: list = dataclasses.field(default_factory=list)  # residual estimates per step
+
+
+def givens(a, b):
+    """Complex Givens (c real, s complex) taking (a, b) to (r e^{i arg a}, 0); b real >= 0."""
+    if a == 0:
+        return 0.0, 1.0 + 0.0j
+    r = np.sqrt(abs(a) ** 2 + abs(b) ** 2)
+    return abs(a) / r, (a / abs(a)) * (b / r)
+
+
+def _rotate(c, s, x, y):
+    return c * x + s * y, -np.conj(s) * x + c * y
+
+
+def gmres(matvec, b, m, tol=1e-10, maxit=10000, precond=None, ortho="cgs2", x0=None):
+    """Restarted right-preconditioned GMRES(m). Returns (x, Stats)."""
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    Minv = precond if precond is not None else (lambda v: v)
+    x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    st = Stats()
+    nb = np.linalg.norm(b)
+    if nb == 0:
+        st.converged, st.relres = True, 0.0
+        return x, st
+    r = b - matvec(x)
+    st.relres = np.linalg.norm(r) / nb
+    if st.relres <= tol:
+        st.converged = True
+        return x, st
+    while True:
+        beta0 = np.linalg.norm(r)
+        V = np.zeros((m + 1, n), dtype=np.complex128)
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta0
+        V[0] = r / beta0
+        j_end = 0
+        for j in range(m):
+            w = matvec(Minv(V[j]))
+            st.iterations += 1
+            if ortho == "cgs2":
+                h = V[: j + 1].conj() @ w
+                w = w - V[: j + 1].T @ h
+                h2 = V[: j + 1].conj() @ w
+                w = w - V[: j + 1].T @ h2
+                h = h + h2
+            else:  # modified Gram-Schmidt
+                h = np.zeros(j + 1, dtype=np.complex128)
+                for i in range(j + 1):
+                    h[i] = np.vdot(V[i], w)
+                    w = w - h[i] * V[i]
+            hn = np.linalg.norm(w)
+            H[: j + 1, j] = h
+            H[j + 1, j] = hn
+            for i in range(j):
+                H[i, j], H[i + 1, j] = _rotate(cs[i], sn[i], H[i, j], H[i + 1, j])
+            cs[j], sn[j] = givens(H[j, j], H[j + 1, j])
+            H[j, j], H[j + 1, j] = _rotate(cs[j], sn[j], H[j, j], H[j + 1, j])
+            g[j], g[j + 1] = _rotate(cs[j], sn[j], g[j], 0.0)
+            est = abs(g[j + 1]) / nb
+            st.history.append(est)
+            j_end = j + 1
+            if hn == 0:
+                st.breakdown = True
+            if est <= tol or hn == 0 or st.iterations >= maxit:
+                break
+            V[j + 1] = w / hn
+        # least squares: R y = g[:j_end], R upper triangular
+        y = np.zeros(j_end, dtype=np.complex128)
+        for i in range(j_end - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1: j_end] @ y[i + 1:]) / H[i, i]
+        x = x + Minv(V[:j_end].T @ y)
+        r = b - matvec(x)
+        st.relres = np.linalg.norm(r) / nb
+        if st.relres <= tol:
+            st.converged = True
+            return x, st
+        if st.iterations >= maxit or st.breakdown:
+            return x, st
+        st.restarts += 1
+
+
+def cocg(matvec, b, tol=1e-10, maxit=100000):
+    """COCG for complex-symmetric A. Returns (x, Stats)."""
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128)
+    st = Stats()
+    nb = np.linalg.norm(b)
+    if nb == 0:
+        st.converged, st.relres = True, 0.0
+        return x, st
+    r = b.copy()
+    while True:
+        p = r.copy()
+        rho = r @ r
+        while st.iterations < maxit:
+            q = matvec(p)
+            st.iterations += 1
+            mu = p @ q
+            if mu == 0 or rho == 0:
+                st.breakdown = True
+                break
+            alpha = rho / mu
+            x = x + alpha * p
+            r = r - alpha * q
+            est = np.linalg.norm(r) / nb
+            st.history.append(est)
+            if est <= tol:
+                break
+            rho_new = r @ r
+            p = r + (rho_new / rho) * p
+            rho = rho_new
+        r = b - matvec(x)
+        st.relres = np.linalg.norm(r) / nb
+        if st.relres <= tol:
+            st.converged = True
+            return x, st
+        if st.iterations >= maxit or st.breakdown:
+            return x, st
+        st.restarts += 1
