@@ -1,0 +1,392 @@
+"""Benchmark: frequency-response sweep throughput on GB300 (one JSON line on stdout).
+
+Workload (default "sweep256"): 256 log-spaced frequencies 20-500 Hz, each solved on its own
+wavelength-scaled 2.5 x 1.4 x 1.2 m cabin lattice (24x14x12 .. 148x83x71 bricks, 25.17 M nodes
+in total) with the sun-roof Dirichlet pressure and random seat admittances, to a true FP64
+relative residual of 1e-10. One step = assembly + lifting + solve of all 256 systems in one
+call (helm_solve_batch: one persistent cooperative launch), batched + mixed precision
+(complex64 inner COCG, FP64 refinement). Inputs (lattices, boundary data) are resident on the
+device before timing; the 13 GB of matrices the step assembles exceed L2, so no flush is needed.
+
+Extra measurements in the same line: the plain FP64 solver on the same sweep (batched and
+one-frequency-at-a-time), the SpMV roofline on the 2,203,161-node lattice (complex128 and
+complex64, L2 flushed), the end-to-end figure through host buffers, and the CPU oracle on a
+bounded sample (cpu_baseline). `--impl reference` times the CPU oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import helm_inputs as hi  # noqa: E402
+
+METRIC = "FRF freqs/s at rel-res 1e-10: batched+mixed vs plain FP64; SpMV % HBM roofline"
+TOL = 1e-10
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic bytes (what each solver step must move)
+# ---------------------------------------------------------------------------------------------
+
+def spmv_bytes(n, nnz, vb):
+    """CSR SpMV: values + int32 columns + rowptr + x read once + y written once."""
+    return nnz * (vb + 4) + (n + 1) * 4 + 2 * vb * n
+
+
+def cocg_fp64_bytes(n, nnz, st):
+    it, chk = st["iterations"], st["restarts"] + 1
+    per_it = spmv_bytes(n, nnz, 16) + 96 * n + 48 * n      # SpMV, x/r update, p update
+    check = spmv_bytes(n, nnz, 16) + 32 * n                 # b read, r written
+    return it * per_it + chk * check + 48 * n               # + init (b read, x and r written)
+
+
+def cocg_mixed_bytes(n, nnz, st):
+    it, outer = st["iterations"], st["outer"]
+    inner = spmv_bytes(n, nnz, 8) + 48 * n + 24 * n         # c64 SpMV, x/r update, p update
+    resid = spmv_bytes(n, nnz, 16) + 32 * n                 # FP64 true residual
+    return it * inner + (outer + 1) * resid + outer * (32 * n + 40 * n) + 48 * n
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def build_sweep(nfreq, helm, torch):
+    freqs = hi.sweep_freqs(256)
+    if nfreq < 256:
+        freqs = freqs[np.linspace(0, 255, nfreq).round().astype(int)]
+    probs = [hi.cabin_problem(*hi.sweep_mesh_dims(f)) for f in freqs]
+    ctxs = []
+    for pr in probs:
+        m = pr.mesh
+        c = helm.Context(m.nx, m.ny, m.nz, m.Lx, m.Ly, m.Lz)
+        c.set_boundary(torch.from_numpy(pr.beta).cuda(), torch.from_numpy(pr.dir_nodes).cuda(),
+                       torch.from_numpy(pr.p_dir).cuda())
+        ctxs.append(c)
+    outs = [torch.empty(c.n, dtype=torch.complex128, device="cuda") for c in ctxs]
+    return freqs, probs, ctxs, outs
+
+
+def mixed_opts(helm):
+    return helm.make_opts("cocg", tol=TOL, maxit=400000, mixed=True, inner_tol=1e-4, inner_maxit=60000, max_outer=40)
+
+
+def fp64_opts(helm):
+    return helm.make_opts("cocg", tol=TOL, maxit=400000)
+
+
+def timed(fn, torch, K, W, dist=None):
+    for _ in range(W):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(s)
+    outs = [fn() for _ in range(K)]
+    e1.record(s)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist is not None:
+        dist.barrier()
+    return e0.elapsed_time(e1) / 1000.0, wall, outs
+
+
+def spmv_roofline(helm, torch, peak_gbs):
+    """helm_spmv on the 2,203,161-node lattice, complex128 and complex64, L2 flushed between reps."""
+    pr = hi.cabin_problem(200, 112, 96)
+    m = pr.mesh
+    ctx = helm.Context(m.nx, m.ny, m.nz, m.Lx, m.Ly, m.Lz)
+    ctx.set_boundary(torch.from_numpy(pr.beta).cuda(), torch.from_numpy(pr.dir_nodes).cuda(),
+                     torch.from_numpy(pr.p_dir).cuda())
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, prec, dt, vb in (("c128", helm.HELM_C128, torch.complex128, 16), ("c64", helm.HELM_C64, torch.complex64, 8)):
+        A = helm.helm_assemble(ctx, 250.0, prec, with_rhs=False)
+        x = torch.randn(ctx.n, dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            helm.helm_spmv(A, x, y)
+        times = []
+        s = torch.cuda.current_stream()
+        for _ in range(10):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            helm.helm_spmv(A, x, y)
+            e1.record(s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1000.0)
+        b = spmv_bytes(ctx.n, ctx.nnz, vb)
+        best, med = min(times), statistics.median(times)
+        out[name] = {"n": ctx.n, "nnz": ctx.nnz, "bytes": b, "best_ms": best * 1e3, "median_ms": med * 1e3,
+                     "gbs_best": b / best / 1e9, "gbs_median": b / med / 1e9, "frac_median": b / med / 1e9 / peak_gbs}
+        A.free()
+    ctx.close()
+    return out
+
+
+def cpu_oracle_sample(budget_s=20.0, nfreq=256):
+    """The CPU oracle (numpy/scipy COCG) on every 16th frequency of the sweep, ascending, until
+    the time budget is spent. Returns (freqs done, seconds, cores, description)."""
+    import scipy.sparse  # noqa: F401
+    from oracle import fem, krylov
+    freqs = hi.sweep_freqs(256)
+    if nfreq < 256:
+        freqs = freqs[np.linspace(0, 255, nfreq).round().astype(int)]
+    sample = list(range(0, len(freqs), 16))
+    done, t_total = [], 0.0
+    for k in sample:
+        f = freqs[k]
+        pr = hi.cabin_problem(*hi.sweep_mesh_dims(f))
+        t0 = time.perf_counter()
+        A, b = fem.system(pr, f)
+        x, st = krylov.cocg(lambda v: A @ v, b, tol=TOL, maxit=400000)
+        t_total += time.perf_counter() - t0
+        done.append((float(f), st.iterations, bool(st.converged)))
+        if t_total >= budget_s:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    desc = ("oracle COCG (FP64, numpy/scipy, assembly included) on every 16th sweep frequency from 20 Hz "
+            "upward until %.0f s: %d frequencies (%.1f-%.1f Hz); low frequencies have the smallest "
+            "lattices, so this overstates the oracle's full-sweep rate" % (budget_s, len(done), done[0][0], done[-1][0]))
+    return done, t_total, cores, desc
+
+
+def run_gpu(args):
+    import torch
+    from paper_2112_00087_gb300 import helm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    peaks, peak_kind = measured_peaks()
+    peak_gbs = float(peaks["hbm_gbs"])
+
+    freqs, probs, ctxs, outs = build_sweep(args.nfreq, helm, torch)
+    nsys = len(ctxs)
+    mo = mixed_opts(helm)
+
+    def step():
+        _, st = helm.helm_solve_batch(ctxs, freqs, mo, outs, raise_on_fail=False)
+        return st, helm.helm_last_profile()
+
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks.start()
+    secs, wall, results = timed(step, torch, args.steps, 0, dist)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = t.item()
+    stats, prof = results[-1]
+    n_ok = sum(1 for s in stats if s["status"] == 0)
+    value = world * nsys * args.steps / secs
+
+    # roofline of the dominant kernel (the persistent solve), from the last timed step
+    alg = sum(cocg_mixed_bytes(c.n, c.nnz, s) for c, s in zip(ctxs, stats))
+    kern_s = prof["solve_ms"] / 1e3
+    achieved = alg / kern_s / 1e9
+    launches = sum(p["launches"] for _, p in results)
+
+    out = {"metric": METRIC, "value": value, "unit": "freqs/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64-inner/c128-outer", "data": "synthetic",
+           "config": {"workload": "sweep256: %d log-spaced frequencies 20-500 Hz, each on its own wavelength-scaled "
+                                  "2.5x1.4x1.2 m cabin lattice (24x14x12..148x83x71, %d nodes total), sun-roof "
+                                  "Dirichlet pressure + random seat admittance; COCG, complex64 inner / FP64 "
+                                  "refinement, true rel-res 1e-10; batched in one persistent launch" %
+                                  (nsys, sum(c.n for c in ctxs)),
+                      "l2": "inputs larger than L2 (%.1f GB of CSR assembled per step)" %
+                            (sum(c.nnz * 32 for c in ctxs) / 1e9),
+                      "parallelism": "replicas" if world > 1 else "1 GPU"},
+           "converged": "%d/%d" % (n_ok, nsys),
+           "iterations": {"inner_total": int(sum(s["iterations"] for s in stats)),
+                          "max": int(max(s["iterations"] for s in stats)),
+                          "outer_max": int(max(s["outer"] for s in stats)),
+                          "relres_max": max(s["relres"] for s in stats)},
+           "phases_ms": {"assemble": prof["assemble_ms"], "solve": prof["solve_ms"]},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                        "frac": achieved / peak_gbs, "traffic": None,
+                        "kernel": "cocg_persistent<mixed>", "algorithmic_bytes": alg,
+                        "kernel_ms": prof["solve_ms"], "peak_kind": peak_kind},
+           "gpu_launches": int(launches), "clocks": clk}
+
+    if rank == 0 and not args.quick:
+        # plain FP64 on the same sweep: batched (one launch) and one frequency at a time
+        fo = fp64_opts(helm)
+        t0 = time.perf_counter()
+        torch.cuda.synchronize()
+        _, st64 = helm.helm_solve_batch(ctxs, freqs, fo, outs, raise_on_fail=False)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        prof64 = helm.helm_last_profile()
+        alg64 = sum(cocg_fp64_bytes(c.n, c.nnz, s) for c, s in zip(ctxs, st64))
+        res = {"batched_freqs_per_s": nsys / t_b, "converged": sum(1 for s in st64 if s["status"] == 0),
+               "iterations_total": int(sum(s["iterations"] for s in st64)),
+               "kernel_gbs": alg64 / (prof64["solve_ms"] / 1e3) / 1e9}
+        if not args.no_sequential:
+            t0 = time.perf_counter()
+            for c, f, o in zip(ctxs, freqs, outs):
+                helm.helm_solve_batch([c], [f], fo, [o], raise_on_fail=False)
+            torch.cuda.synchronize()
+            res["sequential_freqs_per_s"] = nsys / (time.perf_counter() - t0)
+        out["plain_fp64"] = res
+        out["speedup_mixed_vs_fp64_batched"] = value / res["batched_freqs_per_s"]
+        out["spmv"] = spmv_roofline(helm, torch, peak_gbs)
+
+        # end to end through host buffers: boundary data in from pinned memory, pressures out
+        hb = [(torch.from_numpy(p.beta).pin_memory(), torch.from_numpy(p.dir_nodes).pin_memory(),
+               torch.from_numpy(p.p_dir).pin_memory()) for p in probs]
+        hout = [torch.empty(c.n, dtype=torch.complex128).pin_memory() for c in ctxs]
+        h2d = sum(b.numel() * 16 + d.numel() * 4 + q.numel() * 16 for b, d, q in hb)
+        d2h = sum(c.n * 16 for c in ctxs)
+
+        def e2e_step():
+            for c, (b, d, q) in zip(ctxs, hb):
+                c.set_boundary(b.cuda(non_blocking=True), d.cuda(non_blocking=True), q.cuda(non_blocking=True))
+            helm.helm_solve_batch(ctxs, freqs, mo, outs, raise_on_fail=False)
+            for o, h in zip(outs, hout):
+                h.copy_(o, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            e2e_step()
+        e2e_s = (time.perf_counter() - t0) / max(1, args.steps)
+        out["e2e"] = {"value": nsys / e2e_s, "unit": "freqs/s", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+    if rank == 0 and not args.no_cpu:
+        done, t_cpu, cores, desc = cpu_oracle_sample(args.cpu_budget, args.nfreq)
+        out["cpu_baseline"] = {"value": len(done) / t_cpu, "unit": "freqs/s", "cores": cores, "kind": "oracle",
+                               "sample": desc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(5.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(per_step, args.nfreq)
+    vals, cores, desc = [], None, None
+    for _ in range(args.steps):
+        done, t, cores, desc = cpu_oracle_sample(per_step, args.nfreq)
+        vals.append((len(done), t))
+    nf = sum(v[0] for v in vals)
+    tt = sum(v[1] for v in vals)
+    value = nf / tt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "freqs/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": tt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": "sweep256 (bounded sample per step, see cpu_baseline.sample)"},
+           "cpu_baseline": {"value": value, "unit": "freqs/s", "cores": cores, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": "freqs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nfreq", type=int, default=256, help="frequencies of the sweep (256 = full workload)")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 / SpMV / e2e comparison legs")
+    ap.add_argument("--no-sequential", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

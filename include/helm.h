@@ -1,0 +1,202 @@
+/*
+ * helm.h -- C ABI of the GB300 cavity-Helmholtz frequency-response library (libhelm.so).
+ *
+ * Problem (paper Sec. 3.2, Helmholtz equation): the time-harmonic acoustic pressure p in a
+ * closed cavity satisfies -w^2 p - c^2 lap(p) = 0; the pressure fluctuation computed over the
+ * sun-roof opening is imposed as Dirichlet data there. Discretised with trilinear (Q1) bricks
+ * on a box lattice, each frequency f (k = 2 pi f / c) gives the complex symmetric system
+ *
+ *     (K - k^2 M + i k rho c B(beta)) p = 0   with p = p_D on the Dirichlet nodes,
+ *
+ * K the stiffness, M the mass, B(beta) = sum_e beta_e B_e the admittance (wall) term over
+ * boundary quads e (quad mass B_e, beta_e complex, 0 = rigid). Sign reading: e^{+i w t}, so
+ * Re(beta) > 0 absorbs. The Dirichlet nodes are eliminated symmetrically: their rows and
+ * columns become identity rows/columns and b_F = -A_FD p_D, b_D = p_D, so the matrix stays
+ * complex symmetric (A == A^T). Paper Sec. 4: the system is stored in CSR and solved by Krylov
+ * methods in complex double precision on the GPU.
+ *
+ * Numbering (shared with every caller):
+ *   node id       = i + (nx+1) * (j + (ny+1) * l),  0<=i<=nx, 0<=j<=ny, 0<=l<=nz, z vertical;
+ *   boundary quads: sides in the order x-, x+, y-, y+, z-, z+; inside a side the quad at
+ *                   in-plane element indices (u, v) is u + nu * v, u the first remaining axis
+ *                   (x before y before z). n_bface = 2 (ny nz + nx nz + nx ny).
+ *   CSR pattern   : full 27-point pattern of the lattice, columns ascending in every row;
+ *                   entries forced to zero by the elimination stay as explicit zeros.
+ *
+ * Complex data are interleaved (re, im) pairs: double[2] for complex128, float[2] for
+ * complex64 -- the layout of torch.complex128 / torch.complex64.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked (dev) are device pointers of the current CUDA device, (host) host ones.
+ *   - The caller owns every buffer it passes; the library owns helm_ctx / helm_matrix and the
+ *     scratch they allocate (freed by helm_destroy / helm_matrix_free).
+ *   - Work is ordered on the stream given to helm_create (or to helm_spmv); calls return
+ *     without synchronising unless stated otherwise.
+ *   - A non-HELM_OK status comes with a message from helm_last_error(). No C++ exception
+ *     crosses this boundary. Argument errors are detected before any device work is queued.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { int32_t nx, ny, nz; double Lx, Ly, Lz; } helm_mesh_desc; /* box lattice, metres */
+typedef struct { double c, rho; } helm_phys;                               /* m/s, kg/m^3 */
+
+typedef enum {
+  HELM_OK = 0,
+  HELM_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad option) */
+  HELM_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  HELM_ERR_OOM = 3,        /* device allocation failed */
+  HELM_NOT_CONVERGED = 4,  /* solve hit maxit; best iterate and stats are still written */
+  HELM_BREAKDOWN = 5,      /* Krylov breakdown (COCG p^T A p == 0 or r^T r == 0) */
+  HELM_NAN = 6,            /* non-finite residual */
+  HELM_PIVOT = 7,          /* Schwarz local factorisation met a pivot below threshold */
+  HELM_TIMEOUT = 8,        /* a device-side wait gave up (bounded barrier) */
+  HELM_ERR_STATE = 9       /* call out of order (e.g. solve before helm_set_boundary) */
+} helm_status;
+
+enum { HELM_C128 = 0, HELM_C64 = 1 };                 /* matrix value precision */
+enum { HELM_SOLVER_GMRES = 0, HELM_SOLVER_COCG = 1 }; /* Krylov method */
+enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1 }; /* right preconditioner (GMRES only) */
+
+typedef struct {
+  int32_t solver;       /* HELM_SOLVER_GMRES: restarted GMRES(restart), CGS2 Arnoldi, complex
+                           Givens; HELM_SOLVER_COCG: conjugate-orthogonal CG (A complex symmetric) */
+  int32_t restart;      /* GMRES cycle length m (1..128) */
+  double tol;           /* stop when the true ||b - A p||_2 / ||b||_2 <= tol */
+  int32_t maxit;        /* Krylov steps (SpMVs inside the iteration) before HELM_NOT_CONVERGED */
+  int32_t precond;      /* HELM_PRECOND_NONE or HELM_PRECOND_RAS (GMRES only) */
+  int32_t ras_parts[3]; /* Schwarz blocks along x, y, z */
+  int32_t ras_overlap;  /* lattice layers of overlap */
+  int32_t mixed;        /* 1: FP64 iterative refinement around a complex64 inner COCG (COCG only) */
+  double inner_tol;     /* mixed: inner relative residual reduction per refinement step */
+  int32_t inner_maxit;  /* mixed: inner steps per refinement step */
+  int32_t max_outer;    /* mixed: refinement steps before HELM_NOT_CONVERGED */
+} helm_solve_opts;
+
+typedef struct {
+  int32_t status;       /* helm_status of this system */
+  int32_t iterations;   /* Krylov steps (inner complex64 steps when mixed) */
+  int32_t restarts;     /* GMRES cycles - 1 / COCG residual-replacement restarts */
+  int32_t outer;        /* mixed: refinement steps taken */
+  double relres;        /* true FP64 ||b - A p|| / ||b|| at exit */
+  double bnorm;         /* ||b||_2 */
+} helm_solve_stats;
+
+typedef struct {
+  double assemble_ms;   /* device time of the assembly / lifting / cast kernels of the last solve */
+  double solve_ms;      /* device time of the Krylov kernels of the last solve (CUDA events on
+                           the solve stream around the persistent launch / the GMRES cycles) */
+  int64_t launches;     /* kernels this library launched in the last solve call */
+  int32_t grid_blocks;  /* blocks of the persistent launch (0 for GMRES) */
+  int32_t ntiles;       /* row tiles of the persistent launch */
+} helm_profile;
+
+typedef struct helm_ctx helm_ctx;       /* one lattice + physics + boundary data */
+typedef struct helm_matrix helm_matrix; /* one assembled, eliminated system matrix (CSR) */
+
+/* Last error message of the calling thread ("" if none). Owned by the library. */
+const char* helm_last_error(void);
+
+/* Create a context for the lattice `mesh` (nx,ny,nz >= 1, lengths > 0) and physics `phys`,
+ * ordering its work on `stream` (a cudaStream_t, NULL = legacy default stream). */
+helm_status helm_create(helm_ctx** out, const helm_mesh_desc* mesh, const helm_phys* phys,
+                        void* stream);
+void helm_destroy(helm_ctx* ctx);
+
+/* Boundary data (paper Sec. 3.2: sun-roof pressure as Dirichlet data; walls by admittance).
+ *   beta_face (dev) complex128 [n_bface]: admittance per boundary quad, 0 = rigid; may be NULL
+ *                   (all rigid).
+ *   dir_nodes (dev) int32 [n_dir]: distinct node ids with prescribed pressure, any order.
+ *   p_dir     (dev) complex128 [n_dir]: the prescribed pressure at dir_nodes.
+ * The library copies the data; the caller may free its buffers after the call returns and
+ * the stream has passed it. n_dir may be 0 (pure admittance problem). */
+helm_status helm_set_boundary(helm_ctx* ctx, const double* beta_face, const int32_t* dir_nodes,
+                              int32_t n_dir, const double* p_dir);
+
+/* Sizes of the context's lattice. Any output pointer may be NULL. */
+helm_status helm_sizes(const helm_ctx* ctx, int64_t* n_nodes, int64_t* nnz, int64_t* n_bface,
+                       int32_t* n_dir);
+
+/* Assemble the eliminated system matrix at frequency freq_hz (paper Sec. 3.2 Helmholtz eq.,
+ * Sec. 4 CSR storage) in `precision` (HELM_C128 or HELM_C64: complex64 values rounded from the
+ * complex128 ones). If b_out (dev, complex128 [n]) is not NULL the lifted right-hand side
+ * b_F = -A_FD p_D, b_D = p_D is written there. *A_out is owned by the caller's handle until
+ * helm_matrix_free. */
+helm_status helm_assemble(helm_ctx* ctx, double freq_hz, int32_t precision, helm_matrix** A_out,
+                          double* b_out);
+void helm_matrix_free(helm_matrix* A);
+
+/* Read-only views of an assembled matrix: rowptr (dev int32 [n+1]), col (dev int32 [nnz]),
+ * val (dev complex [nnz], complex128 or complex64 per precision). Any pointer may be NULL. */
+helm_status helm_matrix_csr(const helm_matrix* A, int64_t* n, int64_t* nnz, int32_t* precision,
+                            const int32_t** rowptr, const int32_t** col, const void** val);
+
+/* y = A x (paper Sec. 4: "the most time consuming operation"). x, y (dev) complex [n] in the
+ * matrix precision (complex64 matrices accumulate in FP32), must not overlap. Ordered on
+ * `stream` (cudaStream_t; NULL = the context stream of the matrix). */
+helm_status helm_spmv(const helm_matrix* A, const void* x, void* y, void* stream);
+
+/* Reductions over complex128 vectors x, y (dev, [n]), FP64 accumulation in a fixed order:
+ * op 0: x^H y (conjugated, GMRES), op 1: x^T y (unconjugated, COCG), op 2: ||x||_2 (y unused).
+ * The result (host, double[2]) is written after the call synchronises `stream`. */
+helm_status helm_reduce(int32_t op, int64_t n, const double* x, const double* y, double* out,
+                        void* stream);
+
+/* Frequency response: solve the system of every frequency freqs_hz[0..nfreq) (host) on the
+ * context's lattice. p_out (dev, complex128 [nfreq][n]) receives the pressure (the best
+ * iterate if not converged); stats (host, [nfreq]) the per-frequency statistics. COCG systems
+ * (FP64 or mixed) advance together in one persistent cooperative launch; GMRES systems run
+ * one after another, each restart cycle a captured CUDA graph. Synchronises the stream.
+ * Returns HELM_OK if every system converged, else the first failing status. */
+helm_status helm_solve(helm_ctx* ctx, const double* freqs_hz, int32_t nfreq,
+                       const helm_solve_opts* opts, double* p_out, helm_solve_stats* stats);
+
+/* Batched frequency-response sweep over systems that may live on different lattices:
+ * system s is context ctxs[s] (host array) at frequency freqs_hz[s] (host); its pressure goes
+ * to p_out[s] (host array of dev pointers, complex128 [n_s]). COCG only (FP64 or mixed); all
+ * systems advance together in one persistent cooperative launch. Synchronises the first
+ * context's stream. */
+helm_status helm_solve_batch(helm_ctx* const* ctxs, const double* freqs_hz, int32_t nsys,
+                             const helm_solve_opts* opts, double* const* p_out,
+                             helm_solve_stats* stats);
+
+/* Adjoint gradient of the listener objective J = sum_f sum_i w_i |p_i(f)|^2.
+ *   p      (dev) complex128 [nfreq][n]: forward pressures from helm_solve at freqs_hz.
+ *   w_node (dev) float64 [n]: listener weights (e.g. 1/|S| inside the listener region).
+ * Because A is complex symmetric the adjoint system is A lam = W conj(p), solved with
+ * `opts` (same solver as the forward solve). Outputs (PyTorch convention for a real loss:
+ * d/dRe + i d/dIm), summed over frequencies:
+ *   grad_beta (dev) complex128 [n_bface]: -2 conj(lam_F^T (i k rho c B_e) p) per boundary quad;
+ *   grad_pdir (dev) complex128 [n_dir]  :  2 conj(W_D conj(p_D) - A_DF lam_F) per Dirichlet node
+ *                                          (in the order given to helm_set_boundary);
+ *   J_out     (host, may be NULL)       : the objective.
+ * Synchronises the stream. */
+helm_status helm_adjoint_grad(helm_ctx* ctx, const double* freqs_hz, int32_t nfreq,
+                              const helm_solve_opts* opts, const double* p, const double* w_node,
+                              double* grad_beta, double* grad_pdir, double* J_out);
+
+/* Timing record of the calling thread's last helm_solve / helm_solve_batch (host, written). */
+helm_status helm_last_profile(helm_profile* out);
+
+/* Adjoint gradient for any real loss L(p) of the pressures (the backward step of an autograd
+ * wrapper). grad_p (dev, complex128 [nfreq][n]) is PyTorch's gradient of L with respect to
+ * p = helm_solve's output (dL/dRe p + i dL/dIm p). With lam = A^-1 conj(grad_p) (one adjoint
+ * solve per frequency, A complex symmetric) and lam_F = lam zeroed on the Dirichlet nodes:
+ *   grad_beta (dev, complex128 [n_bface]) += -conj(lam_F^T (i k rho c B_e) p) per boundary quad;
+ *   grad_pdir (dev, complex128 [n_dir])   +=  conj(lam_D - A_DF lam_F) per Dirichlet node;
+ * both overwritten (not accumulated across calls), summed over frequencies. helm_adjoint_grad is
+ * this call with grad_p = 2 w p. Synchronises the stream. */
+helm_status helm_adjoint_seed(helm_ctx* ctx, const double* freqs_hz, int32_t nfreq,
+                              const helm_solve_opts* opts, const double* p, const double* grad_p,
+                              double* grad_beta, double* grad_pdir);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

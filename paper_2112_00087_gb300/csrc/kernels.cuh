@@ -1,0 +1,144 @@
+// Device building blocks shared by the SpMV, reduction and Krylov kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace helm {
+
+constexpr int kBlock = 256;  // threads per block of every row-parallel kernel
+
+// Streaming (evict-first) loads for matrix data read once per product.
+__device__ __forceinline__ cd ld_stream(const cd* p) {
+  double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  return cd(v.x, v.y);
+}
+__device__ __forceinline__ cf ld_stream(const cf* p) {
+  float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+  return cf(v.x, v.y);
+}
+// L2-only loads for values other blocks wrote during the same launch (partials).
+__device__ __forceinline__ cd ld_l2(const cd* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return cd(v.x, v.y);
+}
+
+// One CSR row times a vector, computed by a group of G consecutive lanes (G | 32): lane g of
+// the group takes entries k = start + g, start + g + G, ...; the G partial sums are combined
+// by xor shuffles, so every lane of the group returns the row sum. Entries with a zero
+// imaginary part (all rows away from admittance walls) skip the two imaginary products --
+// the result is identical to the full complex product for finite x. `x` is read with
+// ordinary (coherent) loads because persistent kernels rewrite it between phases.
+// All 32 lanes of the warp must call this together (valid = false rows contribute zero).
+template <int G, typename T>
+__device__ __forceinline__ cplx<T> csr_row(const int32_t* __restrict__ rowptr,
+                                           const int32_t* __restrict__ col,
+                                           const cplx<T>* __restrict__ val, const cplx<T>* x,
+                                           int64_t row, bool valid, int g) {
+  cplx<T> acc(T(0), T(0));
+  if (valid) {
+    const int k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
+    for (int k = k0 + g; k < k1; k += G) {
+      const cplx<T> a = ld_stream(val + k);
+      const int c = __ldcs(col + k);
+      const cplx<T> xv = x[c];
+      acc.re = fma(a.re, xv.re, acc.re);
+      acc.im = fma(a.re, xv.im, acc.im);
+      if (a.im != T(0)) {
+        acc.re = fma(-a.im, xv.im, acc.re);
+        acc.im = fma(a.im, xv.re, acc.im);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+  }
+  return acc;
+}
+
+// Deterministic block sum of NV doubles per thread (fixed shuffle tree, then warps in order).
+// Every thread gets the result. `sh` must hold NV * (kBlock/32) doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q * (kBlock / 32) + w] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kBlock / 32; ++i) s += sh[q * (kBlock / 32) + i];
+    v[q] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Bounded grid barrier for cooperative (co-resident) launches. Arrival: fence, then one atomic
+// per block; the last arriver resets the count and bumps the generation. Waiters spin on the
+// generation with an acquire load, give up after kSpinLimit polls or kTimeoutNs nanoseconds,
+// record DEV_TIMEOUT in the status word and return false so the kernel can unwind.
+// ---------------------------------------------------------------------------------------------
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int status;  // DEV_* bits
+  int pad;
+};
+
+constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s
+constexpr unsigned kSpinLimit = 200000000u;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire(&bar->gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer();
+      unsigned spins = 0;
+      while (ld_acquire(&bar->gen) == g) {
+        ++spins;
+        if (spins > kSpinLimit || ((spins & 1023u) == 0 && globaltimer() - t0 > kTimeoutNs)) {
+          atomicOr(&bar->status, DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*((volatile int*)&bar->status) != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace helm

@@ -1,0 +1,742 @@
+// Batched COCG frequency-response solver in one persistent cooperative launch.
+//
+// Paper Sec. 4 solves the complex double-precision Helmholtz system with Krylov methods on
+// the GPU. For the complex symmetric matrix of the eliminated FE system (A == A^T) the
+// conjugate orthogonal CG (COCG: CG with the unconjugated bilinear form x^T y) is used:
+//   q = A p, alpha = rho / p^T q, x += alpha p, r -= alpha q, rho' = r^T r, beta = rho'/rho,
+//   p = r + beta p;
+// stop when ||r|| / ||b|| <= tol, confirm with the true residual b - A x, restart from x with
+// p = r if it misses tol.
+//
+// Mixed precision (FP64 iterative refinement, complex64 inner solve): r = b - A x in FP64,
+// inner COCG on A d = r / ||r|| with complex64 matrix, vectors and SpMV accumulation, stopped at
+// an inner reduction inner_tol, then x += ||r|| d in FP64. The true residual, the refinement
+// update and the convergence test stay FP64; the inner dot products accumulate in FP64.
+//
+// Every system of the batch (its own lattice, frequency and matrix) is cut into row tiles.
+// One launch runs all systems in lockstep super-steps of three phases (A: SpMV + dot, B: axpys
+// + dots, C: direction update or true residual), separated by bounded grid barriers. Each
+// tile writes its dot-product partials; the last block to finish a system's tiles (atomic
+// arrival count) sums the partials in tile order -- a fixed order, so results do not depend
+// on timing -- and takes that system's scalar decisions. Decisions that end a system take
+// effect only in phase C, so the loop-control values every block reads at the top of a step
+// are stable. Converged systems drop out of a compacted tile list.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace helm {
+namespace {
+
+struct KSys {
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const cd* val;
+  const cf* val32;
+  const cd* b;
+  cd* x;
+  cd* r;
+  cd* p;
+  cd* q;
+  cf* x32;
+  cf* r32;
+  cf* p32;
+  cf* q32;
+  int tile0, ntiles;
+};
+
+enum : int { MODE_RESID = 0, MODE_INNER = 1 };
+enum : int { C_PUPDATE = 0, C_CHECK = 1, C_XUPDATE = 2 };
+
+struct KState {
+  int act;       // 1 while iterating
+  int amode;     // phase A source: 0 = p, 1 = r (and p := r)
+  int cmode;     // phase C action
+  int mode;      // mixed: MODE_RESID / MODE_INNER
+  int it;        // Krylov steps (inner steps when mixed)
+  int inner_it;
+  int outer;
+  int restarts;
+  int status;
+  int bd;        // breakdown seen
+  int pend;      // mixed: finish pending (status in `status`)
+  unsigned arrive;
+  double bnorm, rnorm, relres, est;
+  cd rho, alpha, beta;
+};
+
+struct KTile {
+  int sys;
+  int pad;
+  int64_t row0, row1;
+};
+
+enum : int { CTRL_CUR = 0, CTRL_CNT0 = 1, CTRL_CNT1 = 2, CTRL_NACT = 3, CTRL_FIN = 4, CTRL_N = 8 };
+
+struct KParams {
+  const KSys* sys;
+  KState* st;
+  const KTile* tiles;
+  int ntiles;
+  int* list0;
+  int* list1;
+  int* ctrl;
+  cd* part;  // [ntiles][2]
+  GridBar* bar;
+  double tol;
+  int maxit;
+  double inner_tol;
+  int inner_maxit;
+  int max_outer;
+  int max_steps;
+};
+
+constexpr int G64 = 4;  // lanes per row, complex128 SpMV
+constexpr int G32 = 8;  // lanes per row, complex64 SpMV
+
+__device__ __forceinline__ int vload(const int* p) { return *((volatile const int*)p); }
+
+// Arrival of this block's tile for system s; true (block-uniform) for the last arriver.
+__device__ __forceinline__ bool arrive_last(KState* S, int ntiles_s) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned old = atomicAdd(&S->arrive, 1u);
+    s_last = (old + 1u == (unsigned)ntiles_s);
+    if (s_last) {
+      S->arrive = 0u;
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// Sum of the two complex partials of tiles [tile0, tile0 + nt), tile order, every thread.
+__device__ __forceinline__ void sum_parts(const cd* part, int tile0, int nt, cd& a, cd& b, double* sh) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < nt; t += kBlock) {
+    const cd u = ld_l2(part + 2 * (int64_t)(tile0 + t));
+    const cd w = ld_l2(part + 2 * (int64_t)(tile0 + t) + 1);
+    v[0] += u.re; v[1] += u.im; v[2] += w.re; v[3] += w.im;
+  }
+  block_sum<4>(v, sh);
+  a = cd(v[0], v[1]);
+  b = cd(v[2], v[3]);
+}
+
+__device__ __forceinline__ void write_parts(cd* part, int t, const double (&v)[4]) {
+  if (threadIdx.x == 0) {
+    part[2 * (int64_t)t] = cd(v[0], v[1]);
+    part[2 * (int64_t)t + 1] = cd(v[2], v[3]);
+  }
+}
+
+__device__ __forceinline__ void finish(const KParams& P, KState* S, int status, double relres) {
+  S->status = status;
+  S->relres = relres;
+  S->act = 0;
+  __threadfence();
+  atomicAdd(&P.ctrl[CTRL_FIN], 1);
+  atomicSub(&P.ctrl[CTRL_NACT], 1);
+}
+
+// Block 0, phase A: rebuild the other tile list from the act flags (only when a system
+// finished since the last rebuild). Act flags change only in phase C, so the snapshot is
+// exact. The list index is flipped by the caller in phase B, after every block has read the
+// current index for this step; the new list is consumed from the next step on.
+__device__ bool rebuild_list(const KParams& P, int cur, int& seen_fin, int* sh_int) {
+  const int fin = vload(&P.ctrl[CTRL_FIN]);
+  if (fin == seen_fin) return false;  // block-uniform: every thread read the same stable value
+  seen_fin = fin;
+  int* dst = cur ? P.list0 : P.list1;
+  int base = 0;
+  for (int t0 = 0; t0 < P.ntiles; t0 += kBlock) {
+    const int t = t0 + threadIdx.x;
+    const int keep = (t < P.ntiles) ? vload(&P.st[P.tiles[t].sys].act) : 0;
+    // block exclusive scan of keep (warp ballots, then warp counts in order)
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh_int[w] = __popc(m);
+    __syncthreads();
+    int off = base;
+    for (int i = 0; i < w; ++i) off += sh_int[i];
+    int tot = 0;
+    for (int i = 0; i < kBlock / 32; ++i) tot += sh_int[i];
+    if (keep) dst[off + __popc(m & ((1u << lane) - 1u))] = t;
+    base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.ctrl[cur ? CTRL_CNT0 : CTRL_CNT1] = base;
+    __threadfence();
+  }
+  return true;
+}
+
+// ------------------------------- FP64 COCG phases ---------------------------------------------
+
+__device__ void init_tile(const KParams& P, int t, double* sh, bool mixed) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  const KSys Y = P.sys[T.sys];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+    const cd bi = Y.b[i];
+    Y.x[i] = cd(0.0, 0.0);
+    Y.r[i] = bi;
+    v[0] += bi.re * bi.re - bi.im * bi.im;
+    v[1] += 2.0 * bi.re * bi.im;
+    v[2] += bi.re * bi.re + bi.im * bi.im;
+  }
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd rho, rr;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho, rr, sh);
+    if (threadIdx.x == 0) {
+      S->bnorm = sqrt(rr.re);
+      S->rnorm = S->bnorm;
+      S->rho = rho;
+      S->amode = 1;
+      S->mode = MODE_RESID;
+      if (S->bnorm == 0.0) finish(P, S, HELM_OK, 0.0);
+    }
+  }
+}
+
+__device__ void phaseA_fp64(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  const int amode = vload(&S->amode);
+  const cd* src = amode ? Y.r : Y.p;
+  const int gid = threadIdx.x / G64, g = threadIdx.x % G64;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
+    const int64_t row = base + gid;
+    const bool valid = row < T.row1;
+    const cd s = csr_row<G64, double>(Y.rowptr, Y.col, Y.val, src, row, valid, g);
+    if (valid && g == 0) {
+      Y.q[row] = s;
+      const cd pi = src[row];
+      if (amode) Y.p[row] = pi;
+      v[0] += pi.re * s.re - pi.im * s.im;
+      v[1] += pi.re * s.im + pi.im * s.re;
+    }
+  }
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd mu, unused;
+    sum_parts(P.part, Y.tile0, Y.ntiles, mu, unused, sh);
+    if (threadIdx.x == 0) {
+      S->it += 1;
+      const cd rho = S->rho;
+      if ((mu.re == 0.0 && mu.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0)) {
+        S->bd = 1;
+        S->alpha = cd(0.0, 0.0);
+      } else {
+        S->alpha = cdiv(rho, mu);
+      }
+    }
+  }
+}
+
+__device__ void phaseB_fp64(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  const cd al = S->alpha;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+    const cd pi = Y.p[i], qi = Y.q[i];
+    cd xi = Y.x[i], ri = Y.r[i];
+    cfma(xi, al, pi);
+    cfma(ri, cd(-al.re, -al.im), qi);
+    Y.x[i] = xi;
+    Y.r[i] = ri;
+    v[0] += ri.re * ri.re - ri.im * ri.im;
+    v[1] += 2.0 * ri.re * ri.im;
+    v[2] += ri.re * ri.re + ri.im * ri.im;
+  }
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd rho_new, rr;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho_new, rr, sh);
+    if (threadIdx.x == 0) {
+      const double est = sqrt(rr.re) / S->bnorm;
+      S->est = est;
+      S->amode = 0;
+      if (!(est > P.tol) || S->it >= P.maxit || S->bd) {
+        S->cmode = C_CHECK;
+      } else {
+        S->beta = cdiv(rho_new, S->rho);
+        S->rho = rho_new;
+        S->cmode = C_PUPDATE;
+      }
+    }
+  }
+}
+
+__device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  if (vload(&S->cmode) == C_PUPDATE) {
+    const cd be = S->beta;
+    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+      cd pn = Y.r[i];
+      cfma(pn, be, Y.p[i]);
+      Y.p[i] = pn;
+    }
+    return;
+  }
+  // true residual r = b - A x
+  const int gid = threadIdx.x / G64, g = threadIdx.x % G64;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
+    const int64_t row = base + gid;
+    const bool valid = row < T.row1;
+    const cd s = csr_row<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
+    if (valid && g == 0) {
+      const cd bi = Y.b[row];
+      const cd ri(bi.re - s.re, bi.im - s.im);
+      Y.r[row] = ri;
+      v[0] += ri.re * ri.re - ri.im * ri.im;
+      v[1] += 2.0 * ri.re * ri.im;
+      v[2] += ri.re * ri.re + ri.im * ri.im;
+    }
+  }
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd rho, rr;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho, rr, sh);
+    if (threadIdx.x == 0) {
+      const double rel = sqrt(rr.re) / S->bnorm;
+      S->relres = rel;
+      if (rel <= P.tol) finish(P, S, HELM_OK, rel);
+      else if (!(rel == rel)) finish(P, S, HELM_NAN, rel);
+      else if (S->it >= P.maxit) finish(P, S, HELM_NOT_CONVERGED, rel);
+      else if (S->bd) finish(P, S, HELM_BREAKDOWN, rel);
+      else {
+        S->rho = rho;
+        S->amode = 1;
+        S->restarts += 1;
+      }
+    }
+  }
+}
+
+// ------------------------------- mixed-precision phases ---------------------------------------
+
+__device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (vload(&S->mode) == MODE_RESID) {
+    // FP64 true residual of the refinement
+    const int gid = threadIdx.x / G64, g = threadIdx.x % G64;
+    for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
+      const int64_t row = base + gid;
+      const bool valid = row < T.row1;
+      const cd s = csr_row<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
+      if (valid && g == 0) {
+        const cd bi = Y.b[row];
+        const cd ri(bi.re - s.re, bi.im - s.im);
+        Y.r[row] = ri;
+        v[2] += ri.re * ri.re + ri.im * ri.im;
+      }
+    }
+    block_sum<4>(v, sh);
+    write_parts(P.part, t, v);
+    if (arrive_last(S, Y.ntiles)) {
+      cd u, rr;
+      sum_parts(P.part, Y.tile0, Y.ntiles, u, rr, sh);
+      if (threadIdx.x == 0) {
+        const double rel = sqrt(rr.re) / S->bnorm;
+        S->relres = rel;
+        S->pend = 0;
+        if (rel <= P.tol) { S->pend = 1; S->status = HELM_OK; }
+        else if (!(rel == rel)) { S->pend = 1; S->status = HELM_NAN; }
+        else if (S->outer >= P.max_outer || S->it >= P.maxit) { S->pend = 1; S->status = HELM_NOT_CONVERGED; }
+        else { S->rnorm = sqrt(rr.re); S->outer += 1; }
+      }
+    }
+    return;
+  }
+  // inner complex64 step: q32 = A32 src
+  const int amode = vload(&S->amode);
+  const cf* src = amode ? Y.r32 : Y.p32;
+  const int gid = threadIdx.x / G32, g = threadIdx.x % G32;
+  for (int64_t base = T.row0; base < T.row1; base += kBlock / G32) {
+    const int64_t row = base + gid;
+    const bool valid = row < T.row1;
+    const cf s = csr_row<G32, float>(Y.rowptr, Y.col, Y.val32, src, row, valid, g);
+    if (valid && g == 0) {
+      Y.q32[row] = s;
+      const cf pi = src[row];
+      if (amode) Y.p32[row] = pi;
+      v[0] += (double)(pi.re * s.re - pi.im * s.im);
+      v[1] += (double)(pi.re * s.im + pi.im * s.re);
+    }
+  }
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd mu, unused;
+    sum_parts(P.part, Y.tile0, Y.ntiles, mu, unused, sh);
+    if (threadIdx.x == 0) {
+      S->it += 1;
+      S->inner_it += 1;
+      const cd rho = S->rho;
+      if ((mu.re == 0.0 && mu.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0)) {
+        S->bd = 1;
+        S->alpha = cd(0.0, 0.0);
+      } else {
+        S->alpha = cdiv(rho, mu);
+      }
+    }
+  }
+}
+
+__device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (vload(&S->mode) == MODE_RESID) {
+    if (vload(&S->pend)) return;
+    // start an inner solve on r / ||r|| (complex64), x32 = 0
+    const double sc = 1.0 / S->rnorm;
+    float a0 = 0.f, a1 = 0.f;
+    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+      const cd ri = Y.r[i];
+      const cf r32(__double2float_rn(ri.re * sc), __double2float_rn(ri.im * sc));
+      Y.r32[i] = r32;
+      Y.x32[i] = cf(0.f, 0.f);
+      a0 += r32.re * r32.re - r32.im * r32.im;
+      a1 += 2.f * r32.re * r32.im;
+    }
+    v[0] = a0;
+    v[1] = a1;
+    block_sum<4>(v, sh);
+    write_parts(P.part, t, v);
+    if (arrive_last(S, Y.ntiles)) {
+      cd rho, unused;
+      sum_parts(P.part, Y.tile0, Y.ntiles, rho, unused, sh);
+      if (threadIdx.x == 0) {
+        S->rho = rho;
+        S->amode = 1;
+        S->inner_it = 0;
+        S->bd = 0;
+        S->mode = MODE_INNER;
+      }
+    }
+    return;
+  }
+  const cd al = S->alpha;
+  const cf a32((float)al.re, (float)al.im);
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+    const cf pi = Y.p32[i], qi = Y.q32[i];
+    cf xi = Y.x32[i], ri = Y.r32[i];
+    cfma(xi, a32, pi);
+    cfma(ri, cf(-a32.re, -a32.im), qi);
+    Y.x32[i] = xi;
+    Y.r32[i] = ri;
+    acc[0] += ri.re * ri.re - ri.im * ri.im;
+    acc[1] += 2.f * ri.re * ri.im;
+    acc[2] += ri.re * ri.re + ri.im * ri.im;
+  }
+  v[0] = acc[0];
+  v[1] = acc[1];
+  v[2] = acc[2];
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd rho_new, rr;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho_new, rr, sh);
+    if (threadIdx.x == 0) {
+      const double est = sqrt(rr.re);  // relative to ||r / ||r|| || = 1
+      S->est = est;
+      S->amode = 0;
+      if (!(est > P.inner_tol) || S->inner_it >= P.inner_maxit || S->it >= P.maxit || S->bd) {
+        S->cmode = C_XUPDATE;
+      } else {
+        S->beta = cdiv(rho_new, S->rho);
+        S->rho = rho_new;
+        S->cmode = C_PUPDATE;
+      }
+    }
+  }
+}
+
+__device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  if (vload(&S->mode) == MODE_RESID) {
+    if (!vload(&S->pend)) return;
+    if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) finish(P, S, S->status, S->relres);
+    return;
+  }
+  if (vload(&S->cmode) == C_PUPDATE) {
+    const cd be = S->beta;
+    const cf b32((float)be.re, (float)be.im);
+    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+      cf pn = Y.r32[i];
+      cfma(pn, b32, Y.p32[i]);
+      Y.p32[i] = pn;
+    }
+    return;
+  }
+  // refinement update x += ||r|| * d (FP64)
+  const double sc = S->rnorm;
+  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+    const cf d = Y.x32[i];
+    cd xi = Y.x[i];
+    xi.re = fma(sc, (double)d.re, xi.re);
+    xi.im = fma(sc, (double)d.im, xi.im);
+    Y.x[i] = xi;
+  }
+  if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) S->mode = MODE_RESID;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kBlock, 2) cocg_persistent(KParams P) {
+  __shared__ double sh[4 * (kBlock / 32)];
+  __shared__ int sh_int[kBlock / 32];
+  const unsigned nb = gridDim.x;
+  int seen_fin = 0;
+  for (int t = blockIdx.x; t < P.ntiles; t += nb) init_tile(P, t, sh, MIXED);
+  if (!grid_barrier(P.bar, nb)) return;
+  for (int step = 0; step < P.max_steps; ++step) {
+    if (vload(&P.ctrl[CTRL_NACT]) == 0) break;
+    const int cur = vload(&P.ctrl[CTRL_CUR]);
+    const int nat = vload(&P.ctrl[cur ? CTRL_CNT1 : CTRL_CNT0]);
+    const int* list = cur ? P.list1 : P.list0;
+    bool rebuilt = false;
+    if (blockIdx.x == 0) rebuilt = rebuild_list(P, cur, seen_fin, sh_int);
+    for (int a = blockIdx.x; a < nat; a += nb) {
+      if (MIXED) phaseA_mixed(P, list[a], sh);
+      else phaseA_fp64(P, list[a], sh);
+    }
+    if (!grid_barrier(P.bar, nb)) return;
+    if (rebuilt && threadIdx.x == 0) P.ctrl[CTRL_CUR] = cur ^ 1;
+    for (int a = blockIdx.x; a < nat; a += nb) {
+      if (MIXED) phaseB_mixed(P, list[a], sh);
+      else phaseB_fp64(P, list[a], sh);
+    }
+    if (!grid_barrier(P.bar, nb)) return;
+    for (int a = blockIdx.x; a < nat; a += nb) {
+      if (MIXED) phaseC_mixed(P, list[a], sh);
+      else phaseC_fp64(P, list[a], sh);
+    }
+    if (!grid_barrier(P.bar, nb)) return;
+  }
+}
+
+// Simple bump allocator over one device allocation (256-byte aligned pieces).
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0, cap = 0;
+  template <typename T> T* take(size_t count) {
+    size_t bytes = ((count * sizeof(T)) + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+inline size_t rnd(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+
+}  // namespace
+
+helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_opts& o, cudaStream_t s) {
+  if (nsys <= 0) return HELM_OK;
+  const bool mixed = o.mixed != 0;
+  int dev = 0, nsm = 1;
+  HELM_CUDA(cudaGetDevice(&dev));
+  HELM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int coop = 0;
+  HELM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return set_error(HELM_ERR_CUDA, "device does not support cooperative launch");
+  auto kern = mixed ? cocg_persistent<true> : cocg_persistent<false>;
+  int per_sm = 0;
+  HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+  if (per_sm < 1) return set_error(HELM_ERR_CUDA, "persistent kernel cannot be resident");
+  per_sm = std::min(per_sm, 2);
+  const int nblocks = nsm * per_sm;
+
+  // tiles: about nblocks tiles for a system that fills the GPU, 256-row multiples
+  std::vector<KTile> tiles;
+  std::vector<int> tile0(nsys), ntl(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    const int64_t n = sys[k].ctx->n;
+    const int64_t per = 256 * std::max<int64_t>(1, (n + 256LL * nblocks - 1) / (256LL * nblocks));
+    tile0[k] = (int)tiles.size();
+    for (int64_t r0 = 0; r0 < n; r0 += per) tiles.push_back(KTile{k, 0, r0, std::min(n, r0 + per)});
+    ntl[k] = (int)tiles.size() - tile0[k];
+  }
+  const int ntiles = (int)tiles.size();
+
+  // one arena for every per-system buffer plus the control data
+  size_t bytes = 0;
+  for (int k = 0; k < nsys; ++k) {
+    const size_t n = sys[k].ctx->n, nnz = sys[k].ctx->nnz;
+    bytes += rnd(nnz * sizeof(cd)) + rnd(n * sizeof(cd)) * 2;  // val, b, r
+    if (mixed) bytes += rnd(nnz * sizeof(cf)) + 4 * rnd(n * sizeof(cf));
+    else bytes += 2 * rnd(n * sizeof(cd));  // p, q
+  }
+  bytes += rnd(nsys * sizeof(KSys)) + rnd(nsys * sizeof(KState)) + rnd(ntiles * sizeof(KTile)) +
+           2 * rnd(ntiles * sizeof(int)) + rnd(CTRL_N * sizeof(int)) + rnd(2 * (size_t)ntiles * sizeof(cd)) +
+           rnd(sizeof(GridBar));
+  Arena A;
+  A.cap = bytes;
+  helm_status st = dev_alloc(&A.base, bytes);
+  if (st != HELM_OK) return st;
+
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  for (int q = 0; q < 3; ++q) cudaEventCreate(&ev[q]);
+  cudaEventRecord(ev[0], s);
+  std::vector<KSys> hs(nsys);
+  std::vector<KState> hst(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    const helm_ctx* c = sys[k].ctx;
+    KSys& Y = hs[k];
+    memset(&Y, 0, sizeof(Y));
+    Y.n = c->n;
+    Y.rowptr = c->rowptr;
+    Y.col = c->col;
+    cd* val = A.take<cd>(c->nnz);
+    cd* b = A.take<cd>(c->n);
+    Y.val = val;
+    Y.b = b;
+    Y.x = sys[k].p_out;
+    Y.r = A.take<cd>(c->n);
+    if (mixed) {
+      cf* v32 = A.take<cf>(c->nnz);
+      Y.val32 = v32;
+      Y.x32 = A.take<cf>(c->n);
+      Y.r32 = A.take<cf>(c->n);
+      Y.p32 = A.take<cf>(c->n);
+      Y.q32 = A.take<cf>(c->n);
+    } else {
+      Y.p = A.take<cd>(c->n);
+      Y.q = A.take<cd>(c->n);
+    }
+    Y.tile0 = tile0[k];
+    Y.ntiles = ntl[k];
+    st = assemble_values(c, sys[k].freq, val, b, s);
+    if (st == HELM_OK && sys[k].rhs) {
+      cudaError_t ce = cudaMemcpyAsync(b, sys[k].rhs, c->n * sizeof(cd), cudaMemcpyDeviceToDevice, s);
+      if (ce != cudaSuccess) st = cuda_error(ce, "rhs copy");
+    }
+    if (st == HELM_OK && mixed) st = cast_values(val, const_cast<cf*>(Y.val32), c->nnz, s);
+    if (st != HELM_OK) {
+      cudaFree(A.base);
+      return st;
+    }
+    memset(&hst[k], 0, sizeof(KState));
+    hst[k].act = 1;
+  }
+  KSys* d_sys = A.take<KSys>(nsys);
+  KState* d_st = A.take<KState>(nsys);
+  KTile* d_tiles = A.take<KTile>(ntiles);
+  int* d_l0 = A.take<int>(ntiles);
+  int* d_l1 = A.take<int>(ntiles);
+  int* d_ctrl = A.take<int>(CTRL_N);
+  cd* d_part = A.take<cd>(2 * (size_t)ntiles);
+  GridBar* d_bar = A.take<GridBar>(1);
+  std::vector<int> l0(ntiles);
+  for (int t = 0; t < ntiles; ++t) l0[t] = t;
+  int ctrl[CTRL_N] = {0};
+  ctrl[CTRL_CUR] = 0;
+  ctrl[CTRL_CNT0] = ntiles;
+  ctrl[CTRL_NACT] = nsys;
+  cudaError_t e = cudaSuccess;
+  auto H2D = [&](void* d, const void* h, size_t nb) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, nb, cudaMemcpyHostToDevice, s);
+  };
+  H2D(d_sys, hs.data(), nsys * sizeof(KSys));
+  H2D(d_st, hst.data(), nsys * sizeof(KState));
+  H2D(d_tiles, tiles.data(), ntiles * sizeof(KTile));
+  H2D(d_l0, l0.data(), ntiles * sizeof(int));
+  H2D(d_ctrl, ctrl, sizeof(ctrl));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bar, 0, sizeof(GridBar), s);
+
+  KParams P;
+  P.sys = d_sys;
+  P.st = d_st;
+  P.tiles = d_tiles;
+  P.ntiles = ntiles;
+  P.list0 = d_l0;
+  P.list1 = d_l1;
+  P.ctrl = d_ctrl;
+  P.part = d_part;
+  P.bar = d_bar;
+  P.tol = o.tol;
+  P.maxit = o.maxit;
+  P.inner_tol = o.inner_tol;
+  P.inner_maxit = o.inner_maxit;
+  P.max_outer = o.max_outer;
+  // each super-step advances every active system by one Krylov step, except refinement
+  // residual steps (at most max_outer + 1 of them) and COCG residual checks
+  P.max_steps = 2 * o.maxit + 2 * (o.max_outer + 2) + 16;
+  void* args[] = {&P};
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(nblocks), dim3(kBlock), args, 0, s);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
+  GridBar hb;
+  memset(&hb, 0, sizeof(hb));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), d_st, nsys * sizeof(KState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(A.base);
+  if (e == cudaSuccess) {
+    float t_asm = 0.f, t_solve = 0.f;
+    cudaEventElapsedTime(&t_asm, ev[0], ev[1]);
+    cudaEventElapsedTime(&t_solve, ev[1], ev[2]);
+    helm_profile& pr = last_profile();
+    pr.assemble_ms += t_asm;
+    pr.solve_ms += t_solve;
+    pr.launches += (int64_t)nsys * (mixed ? 2 : 1) + 1;
+    pr.grid_blocks = nblocks;
+    pr.ntiles = ntiles;
+  }
+  for (int q = 0; q < 3; ++q) cudaEventDestroy(ev[q]);
+  if (e != cudaSuccess) return cuda_error(e, "cocg persistent solve");
+
+  helm_status overall = HELM_OK;
+  for (int k = 0; k < nsys; ++k) {
+    helm_solve_stats& S = *sys[k].stats;
+    const KState& K = hst[k];
+    S.status = K.act ? HELM_NOT_CONVERGED : K.status;
+    if (hb.status & DEV_TIMEOUT) S.status = HELM_TIMEOUT;
+    S.iterations = K.it;
+    S.restarts = K.restarts;
+    S.outer = K.outer;
+    S.relres = K.relres;
+    S.bnorm = K.bnorm;
+    if (S.status != HELM_OK && overall == HELM_OK) overall = (helm_status)S.status;
+  }
+  if (hb.status & DEV_TIMEOUT) return set_error(HELM_TIMEOUT, "persistent solver: grid barrier timed out");
+  if (overall != HELM_OK) set_error(overall, "at least one system did not converge");
+  return overall;
+}
+
+}  // namespace helm

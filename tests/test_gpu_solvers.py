@@ -1,0 +1,161 @@
+"""GPU parity of the Krylov solvers (COCG, GMRES(m), RAS, mixed precision, batched sweep,
+adjoint) against the CPU oracle, through the C ABI.
+
+Tolerances: FP64 paths run the same iteration as the oracle, so their iterates agree to
+rel-L2 <= 1e-9 and their Krylov step counts within 5%. Against the exact solution x* the error
+of any iterate with true residual <= tol is bounded by cond(A) * tol, which the mixed-precision
+checks use.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spl
+
+import helm_inputs as hi
+from oracle import adjoint, fem, krylov, ras
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2112_00087_gb300 import helm  # noqa: E402
+from tests.gpu_util import context, rel  # noqa: E402
+
+
+def within5(a, b):
+    return abs(a - b) <= max(1, 0.05 * b)
+
+
+@pytest.mark.parametrize("dims,f", [((20, 16, 12), 100.0), ((13, 7, 5), 230.0), ((30, 20, 14), 310.0)])
+def test_cocg_fp64_matches_oracle(dims, f):
+    prob = hi.small_box_problem(*dims)
+    ctx = context(prob)
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts("cocg", tol=1e-10, maxit=20000))
+    A, b = fem.system(prob, f)
+    x, ost = krylov.cocg(lambda v: A @ v, b, tol=1e-10, maxit=20000)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0 and ost.converged
+    assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
+    assert within5(st[0]["iterations"], ost.iterations), (st[0], ost.iterations)
+    assert rel(g, x) <= 1e-9
+
+
+def test_cocg_multi_frequency_one_launch():
+    prob = hi.cabin_problem(24, 14, 12)
+    ctx = context(prob)
+    freqs = [20.0, 75.0, 140.0, 260.0]
+    p, st = helm.helm_solve(ctx, freqs, helm.make_opts("cocg", tol=1e-10, maxit=20000))
+    KM = fem.assemble_KM(prob.mesh)
+    for k, f in enumerate(freqs):
+        A, b = fem.system(prob, f, KM)
+        x, ost = krylov.cocg(lambda v: A @ v, b, tol=1e-10, maxit=20000)
+        assert st[k]["status"] == 0
+        assert within5(st[k]["iterations"], ost.iterations), (f, st[k], ost.iterations)
+        assert rel(p[k].cpu().numpy(), x) <= 1e-9
+
+
+def test_batch_of_different_meshes():
+    # a slice of the multi-mesh sweep: each frequency on its own wavelength-scaled lattice
+    freqs = [20.0, 180.0, 240.0, 300.0]
+    probs = [hi.cabin_problem(*hi.sweep_mesh_dims(f)) for f in freqs]
+    ctxs = [context(pr) for pr in probs]
+    ps, st = helm.helm_solve_batch(ctxs, freqs, helm.make_opts("cocg", tol=1e-10, maxit=50000))
+    for k, (pr, f) in enumerate(zip(probs, freqs)):
+        A, b = fem.system(pr, f)
+        g = ps[k].cpu().numpy()
+        assert st[k]["status"] == 0
+        assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
+        if pr.mesh.n_nodes < 60000:
+            x, ost = krylov.cocg(lambda v: A @ v, b, tol=1e-10, maxit=50000)
+            assert within5(st[k]["iterations"], ost.iterations)
+            assert rel(g, x) <= 1e-9
+
+
+@pytest.mark.parametrize("dims,f,m", [((20, 16, 12), 100.0, 30), ((13, 7, 5), 230.0, 10)])
+def test_gmres_matches_oracle(dims, f, m):
+    prob = hi.small_box_problem(*dims)
+    ctx = context(prob)
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts("gmres", restart=m, tol=1e-10, maxit=20000))
+    A, b = fem.system(prob, f)
+    x, ost = krylov.gmres(lambda v: A @ v, b, m, tol=1e-10, maxit=20000)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0 and ost.converged
+    assert within5(st[0]["iterations"], ost.iterations), (st[0], ost.iterations)
+    assert st[0]["restarts"] == ost.restarts or within5(st[0]["restarts"], ost.restarts)
+    assert rel(g, x) <= 1e-9
+
+
+@pytest.mark.parametrize("dims,parts,f", [((12, 10, 8), (3, 2, 2), 200.0), ((25, 14, 12), (4, 2, 2), 100.0),
+                                          ((6, 5, 4), (1, 1, 1), 150.0)])
+def test_gmres_ras_matches_oracle(dims, parts, f):
+    prob = hi.cabin_problem(*dims) if dims[0] > 20 else hi.small_box_problem(*dims)
+    ctx = context(prob)
+    o = helm.make_opts("gmres", restart=50, tol=1e-10, maxit=5000, precond="ras", ras_parts=parts, ras_overlap=2)
+    p, st = helm.helm_solve(ctx, [f], o)
+    A, b = fem.system(prob, f)
+    P = ras.RAS(A, prob.mesh, parts=parts, overlap=2)
+    x, ost = krylov.gmres(lambda v: A @ v, b, 50, tol=1e-10, maxit=5000, precond=P)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0 and ost.converged
+    assert within5(st[0]["iterations"], ost.iterations), (st[0], ost.iterations)
+    assert rel(g, x) <= 1e-9
+    if parts == (1, 1, 1):
+        assert st[0]["iterations"] == 1
+
+
+@pytest.mark.parametrize("dims,f", [((20, 16, 12), 100.0), ((40, 22, 19), 150.0)])
+def test_mixed_precision_refinement(dims, f):
+    prob = hi.small_box_problem(*dims) if dims[0] == 20 else hi.cabin_problem(*dims)
+    ctx = context(prob)
+    o = helm.make_opts("cocg", tol=1e-10, maxit=50000, mixed=True, inner_tol=1e-4, inner_maxit=5000, max_outer=30)
+    p, st = helm.helm_solve(ctx, [f], o)
+    A, b = fem.system(prob, f)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0, st
+    assert st[0]["outer"] >= 2
+    # the FP64 true residual of the refined result meets the FP64 target
+    assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
+    xs = spl.spsolve(A.tocsc(), b)
+    # forward error bounded like any iterate at rel-res 1e-10
+    _, ost = krylov.cocg(lambda v: A @ v, b, tol=1e-10)
+    x64 = p.new_empty(p.shape)
+    p64, _ = helm.helm_solve(ctx, [f], helm.make_opts("cocg", tol=1e-10, maxit=50000))
+    e_mixed = rel(g, xs)
+    e_fp64 = rel(p64[0].cpu().numpy(), xs)
+    assert e_mixed <= max(10 * e_fp64, 1e-9), (e_mixed, e_fp64)
+
+
+def test_adjoint_matches_oracle_and_autograd():
+    prob = hi.cabin_problem(10, 7, 6, beta_seed=1, p_scale=0.1)
+    m = prob.mesh
+    w = hi.listener_weights(m, radius=0.45)
+    freqs = [60.0, 110.0]
+    ctx = context(prob)
+    o = helm.make_opts("cocg", tol=1e-13, maxit=20000)
+    p, st = helm.helm_solve(ctx, freqs, o)
+    assert all(s["status"] == 0 for s in st)
+    J, gb, gd = helm.helm_adjoint_grad(ctx, freqs, o, p, torch.from_numpy(w).cuda())
+    Jr, gbr, gdr, _ = adjoint.objective_and_gradient(prob, freqs, w)
+    assert abs(J - Jr) <= 1e-10 * abs(Jr)
+    assert rel(gb.cpu().numpy(), gbr) <= 1e-8
+    assert rel(gd.cpu().numpy(), gdr) <= 1e-8
+    # the autograd wrapper gives the same gradients for the same loss
+    beta = torch.from_numpy(prob.beta).cuda().requires_grad_(True)
+    pd = torch.from_numpy(prob.p_dir).cuda().requires_grad_(True)
+    nodes = torch.from_numpy(prob.dir_nodes.astype(np.int32)).cuda()
+    pp = helm.HelmSolve.apply(ctx, freqs, o, nodes, beta, pd)
+    wt = torch.from_numpy(w).cuda()
+    loss = (wt[None, :] * pp.abs() ** 2).sum()
+    loss.backward()
+    assert abs(loss.item() - Jr) <= 1e-10 * abs(Jr)
+    assert rel(beta.grad.cpu().numpy(), gbr) <= 1e-8
+    assert rel(pd.grad.cpu().numpy(), gdr) <= 1e-8
+
+
+def test_nonconvergence_is_reported_not_raised():
+    prob = hi.small_box_problem()
+    ctx = context(prob)
+    p, st = helm.helm_solve(ctx, [100.0], helm.make_opts("cocg", tol=1e-10, maxit=7), raise_on_fail=False)
+    assert st[0]["status"] == helm.HELM_NOT_CONVERGED and st[0]["iterations"] == 7
+    assert np.isfinite(p.cpu().numpy()).all()
