@@ -20,6 +20,11 @@ by step in complex128 numpy, the two iterations the GPU path runs:
 Iteration count = number of Krylov steps (products with A inside the iteration; the
 true-residual products are not counted).
 
+Inner products and norms are the exactly rounded sums (math.fsum) of the elementwise products,
+the closest floating-point rendering of sum_i x_i y_i. (A BLAS dot accumulates in its own
+blocked order; on these indefinite systems COCG's erratic residual history is sensitive enough
+to that rounding to move the step count by up to ~10%.)
+
 Pinned (tests/test_oracle_krylov.py): solutions equal dense LU (numpy.linalg.solve) on
 small meshes, the discrete duct / rigid-box forced-mode solutions are reproduced to
 round-off, a 1x1x1 Schwarz partition converges in one step, Givens rotations annihilate
@@ -27,8 +32,26 @@ and are unitary. Iteration counts themselves are parity-unpinned (the paper prin
 for these methods).
 """
 import dataclasses
+import math
 
 import numpy as np
+
+
+def dotu(x, y):
+    """x^T y (unconjugated), exactly rounded sum of the rounded products."""
+    p = np.asarray(x) * np.asarray(y)
+    return complex(math.fsum(p.real), math.fsum(p.imag))
+
+
+def dotc(x, y):
+    """x^H y, exactly rounded sum of the rounded products."""
+    return dotu(np.conj(x), y)
+
+
+def nrm2(x):
+    """||x||_2 = sqrt of the exactly rounded sum of |x_i|^2."""
+    x = np.asarray(x)
+    return math.sqrt(math.fsum(x.real * x.real + x.imag * x.imag))
 
 
 @dataclasses.dataclass
@@ -60,17 +83,17 @@ def gmres(matvec, b, m, tol=1e-10, maxit=10000, precond=None, ortho="cgs2", x0=N
     Minv = precond if precond is not None else (lambda v: v)
     x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
     st = Stats()
-    nb = np.linalg.norm(b)
+    nb = nrm2(b)
     if nb == 0:
         st.converged, st.relres = True, 0.0
         return x, st
     r = b - matvec(x)
-    st.relres = np.linalg.norm(r) / nb
+    st.relres = nrm2(r) / nb
     if st.relres <= tol:
         st.converged = True
         return x, st
     while True:
-        beta0 = np.linalg.norm(r)
+        beta0 = nrm2(r)
         V = np.zeros((m + 1, n), dtype=np.complex128)
         H = np.zeros((m + 1, m), dtype=np.complex128)
         cs = np.zeros(m)
@@ -83,17 +106,17 @@ def gmres(matvec, b, m, tol=1e-10, maxit=10000, precond=None, ortho="cgs2", x0=N
             w = matvec(Minv(V[j]))
             st.iterations += 1
             if ortho == "cgs2":
-                h = V[: j + 1].conj() @ w
+                h = np.array([dotc(V[i], w) for i in range(j + 1)])
                 w = w - V[: j + 1].T @ h
-                h2 = V[: j + 1].conj() @ w
+                h2 = np.array([dotc(V[i], w) for i in range(j + 1)])
                 w = w - V[: j + 1].T @ h2
                 h = h + h2
             else:  # modified Gram-Schmidt
                 h = np.zeros(j + 1, dtype=np.complex128)
                 for i in range(j + 1):
-                    h[i] = np.vdot(V[i], w)
+                    h[i] = dotc(V[i], w)
                     w = w - h[i] * V[i]
-            hn = np.linalg.norm(w)
+            hn = nrm2(w)
             H[: j + 1, j] = h
             H[j + 1, j] = hn
             for i in range(j):
@@ -115,7 +138,7 @@ def gmres(matvec, b, m, tol=1e-10, maxit=10000, precond=None, ortho="cgs2", x0=N
             y[i] = (g[i] - H[i, i + 1: j_end] @ y[i + 1:]) / H[i, i]
         x = x + Minv(V[:j_end].T @ y)
         r = b - matvec(x)
-        st.relres = np.linalg.norm(r) / nb
+        st.relres = nrm2(r) / nb
         if st.relres <= tol:
             st.converged = True
             return x, st
@@ -130,33 +153,33 @@ def cocg(matvec, b, tol=1e-10, maxit=100000):
     n = b.shape[0]
     x = np.zeros(n, dtype=np.complex128)
     st = Stats()
-    nb = np.linalg.norm(b)
+    nb = nrm2(b)
     if nb == 0:
         st.converged, st.relres = True, 0.0
         return x, st
     r = b.copy()
     while True:
         p = r.copy()
-        rho = r @ r
+        rho = dotu(r, r)
         while st.iterations < maxit:
             q = matvec(p)
             st.iterations += 1
-            mu = p @ q
+            mu = dotu(p, q)
             if mu == 0 or rho == 0:
                 st.breakdown = True
                 break
             alpha = rho / mu
             x = x + alpha * p
             r = r - alpha * q
-            est = np.linalg.norm(r) / nb
+            est = nrm2(r) / nb
             st.history.append(est)
             if est <= tol:
                 break
-            rho_new = r @ r
+            rho_new = dotu(r, r)
             p = r + (rho_new / rho) * p
             rho = rho_new
         r = b - matvec(x)
-        st.relres = np.linalg.norm(r) / nb
+        st.relres = nrm2(r) / nb
         if st.relres <= tol:
             st.converged = True
             return x, st
