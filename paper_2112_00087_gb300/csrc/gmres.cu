@@ -378,7 +378,21 @@ __global__ void __launch_bounds__(kBlock) gm_residual(GmArgs a) {
 
 helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const int32_t* col, const cd* val,
                                double freq, const cd* b, const helm_solve_opts& o, cd* x, helm_solve_stats* st) {
-  cudaStream_t s = ctx->stream;
+  // The cycle is captured as a CUDA graph, which the legacy default stream does not allow: run
+  // the solve on a private stream ordered after the context stream.
+  cudaStream_t s = nullptr;
+  HELM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e0 = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e0 == cudaSuccess) e0 = cudaEventRecord(ev, ctx->stream);
+    if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(s, ev, 0);
+    if (ev) cudaEventDestroy(ev);
+    if (e0 != cudaSuccess) {
+      cudaStreamDestroy(s);
+      return cuda_error(e0, "gmres stream");
+    }
+  }
   const int64_t n = ctx->n;
   const int m = o.restart;
   int dev = 0, nsm = 1;
@@ -438,7 +452,7 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   cudaError_t e = cudaMallocHost((void**)&hctl, sizeof(GmCtl));
   if (e != cudaSuccess) result = cuda_error(e, "cudaMallocHost");
   if (result == HELM_OK && o.precond == HELM_PRECOND_RAS) {
-    result = ras_create(ctx, rowptr, col, val, o.ras_parts, o.ras_overlap, &ras);
+    result = ras_create(ctx, rowptr, col, val, o.ras_parts, o.ras_overlap, &ras, s);
   }
   if (result == HELM_OK) {
     e = cudaMemsetAsync(dctl, 0, sizeof(GmCtl), s);
@@ -530,6 +544,7 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   if (graph) cudaGraphDestroy(graph);
   if (ras) ras_destroy(ras);
   cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
   if (hctl) cudaFreeHost(hctl);
   cudaFree(dctl);
   cudaFree(ws);

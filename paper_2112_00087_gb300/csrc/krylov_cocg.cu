@@ -441,8 +441,7 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
         S->rho = rho;
         S->amode = 1;
         S->inner_it = 0;
-        S->bd = 0;
-        S->mode = MODE_INNER;
+        S->bd = 0;  // the mode itself changes in phase C (phase C of this step still reads it)
       }
     }
     return;
@@ -490,8 +489,11 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
   if (!vload(&S->act)) return;
   const KSys Y = P.sys[T.sys];
   if (vload(&S->mode) == MODE_RESID) {
-    if (!vload(&S->pend)) return;
-    if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) finish(P, S, S->status, S->relres);
+    const int pend = vload(&S->pend);
+    if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) {
+      if (pend) finish(P, S, S->status, S->relres);
+      else S->mode = MODE_INNER;
+    }
     return;
   }
   if (vload(&S->cmode) == C_PUPDATE) {

@@ -218,7 +218,7 @@ std::vector<std::pair<int, int>> block_ranges(int npts, int parts) {
 }  // namespace
 
 helm_status ras_create(const helm_ctx* ctx, const int32_t* rowptr, const int32_t* col, const cd* val,
-                       const int32_t parts[3], int overlap, RasPrecond** out) {
+                       const int32_t parts[3], int overlap, RasPrecond** out, cudaStream_t s) {
   *out = nullptr;
   const int N[3] = {ctx->mesh.nx + 1, ctx->mesh.ny + 1, ctx->mesh.nz + 1};
   for (int a = 0; a < 3; ++a)
@@ -277,7 +277,6 @@ helm_status ras_create(const helm_ctx* ctx, const int32_t* rowptr, const int32_t
     ras_destroy(P);
     return st;
   }
-  cudaStream_t s = ctx->stream;
   cudaError_t e = cudaMemcpyAsync(P->d_sub, subs.data(), subs.size() * sizeof(RasSub), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->d_status, 0, sizeof(int), s);
   if (e == cudaSuccess)
