@@ -120,11 +120,18 @@ class ClockSampler:
 # GPU arm
 # ---------------------------------------------------------------------------------------------
 
-def build_sweep(nfreq, helm, torch):
-    freqs = hi.sweep_freqs(256)
-    if nfreq < 256:
-        freqs = freqs[np.linspace(0, 255, nfreq).round().astype(int)]
-    probs = [hi.cabin_problem(*hi.sweep_mesh_dims(f)) for f in freqs]
+def build_sweep(nfreq, helm, torch, workload="sweep256"):
+    if workload == "sweep256":
+        freqs = hi.sweep_freqs(256)
+        if nfreq < 256:
+            freqs = freqs[np.linspace(0, 255, nfreq).round().astype(int)]
+        probs = [hi.cabin_problem(*hi.sweep_mesh_dims(f)) for f in freqs]
+    else:  # one lattice, several frequencies (profiling cases)
+        dims = {"cabin2m": (200, 112, 96), "cabin282k": (100, 56, 48)}[workload]
+        lo, hi_ = (100.0, 400.0) if workload == "cabin2m" else (20.0, 200.0)
+        freqs = np.geomspace(lo, hi_, max(1, nfreq))
+        pr = hi.cabin_problem(*dims)
+        probs = [pr] * len(freqs)
     ctxs = []
     for pr in probs:
         m = pr.mesh
@@ -136,12 +143,12 @@ def build_sweep(nfreq, helm, torch):
     return freqs, probs, ctxs, outs
 
 
-def mixed_opts(helm):
-    return helm.make_opts("cocg", tol=TOL, maxit=400000, mixed=True, inner_tol=1e-4, inner_maxit=60000, max_outer=40)
+def mixed_opts(helm, maxit=400000):
+    return helm.make_opts("cocg", tol=TOL, maxit=maxit, mixed=True, inner_tol=1e-4, inner_maxit=60000, max_outer=40)
 
 
-def fp64_opts(helm):
-    return helm.make_opts("cocg", tol=TOL, maxit=400000)
+def fp64_opts(helm, maxit=400000):
+    return helm.make_opts("cocg", tol=TOL, maxit=maxit)
 
 
 def timed(fn, torch, K, W, dist=None):
@@ -238,9 +245,9 @@ def run_gpu(args):
     peaks, peak_kind = measured_peaks()
     peak_gbs = float(peaks["hbm_gbs"])
 
-    freqs, probs, ctxs, outs = build_sweep(args.nfreq, helm, torch)
+    freqs, probs, ctxs, outs = build_sweep(args.nfreq, helm, torch, args.workload)
     nsys = len(ctxs)
-    mo = mixed_opts(helm)
+    mo = mixed_opts(helm, args.maxit) if not args.fp64 else fp64_opts(helm, args.maxit)
 
     def step():
         _, st = helm.helm_solve_batch(ctxs, freqs, mo, outs, raise_on_fail=False)
@@ -264,7 +271,7 @@ def run_gpu(args):
     value = world * nsys * args.steps / secs
 
     # roofline of the dominant kernel (the persistent solve), from the last timed step
-    alg = sum(cocg_mixed_bytes(c.n, c.nnz, s) for c, s in zip(ctxs, stats))
+    alg = sum((cocg_fp64_bytes if args.fp64 else cocg_mixed_bytes)(c.n, c.nnz, s) for c, s in zip(ctxs, stats))
     kern_s = prof["solve_ms"] / 1e3
     achieved = alg / kern_s / 1e9
     launches = sum(p["launches"] for _, p in results)
@@ -292,6 +299,11 @@ def run_gpu(args):
                         "kernel_ms": prof["solve_ms"], "peak_kind": peak_kind},
            "gpu_launches": int(launches), "clocks": clk}
 
+    if args.verbose and rank == 0:
+        for c, f, st_ in zip(ctxs, freqs, stats):
+            print("sys f=%7.2f n=%8d its=%6d outer=%3d restarts=%3d status=%d relres=%.2e" %
+                  (f, c.n, st_["iterations"], st_["outer"], st_["restarts"], st_["status"], st_["relres"]),
+                  file=sys.stderr, flush=True)
     if rank == 0 and not args.quick:
         # plain FP64 on the same sweep: batched (one launch) and one frequency at a time
         fo = fp64_opts(helm)
@@ -381,6 +393,11 @@ def main():
     ap.add_argument("--no-sequential", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--workload", default="sweep256", choices=["sweep256", "cabin2m", "cabin282k"],
+                    help="sweep256 is the benchmark; the one-lattice cases serve profiling")
+    ap.add_argument("--maxit", type=int, default=400000, help="Krylov step cap (profiling captures)")
+    ap.add_argument("--fp64", action="store_true", help="time the plain FP64 solver as the main leg")
+    ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

