@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kBlock) gm_spmv(GmArgs a, const cd* src, int j
   for (int64_t base = r0; base < r1; base += kBlock / G) {
     const int64_t row = base + gid;
     const bool valid = row < r1;
-    const cd s = csr_row<G, double>(a.rowptr, a.col, a.val, src, row, valid, g);
+    const cd s = csr_row27<G, double>(a.rowptr, a.col, a.val, src, row, valid, g);
     if (valid && g == 0) a.w[row] = s;
   }
 }
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kBlock) gm_residual(GmArgs a) {
   for (int64_t base = r0; base < r1; base += kBlock / G) {
     const int64_t row = base + gid;
     const bool valid = row < r1;
-    const cd s = csr_row<G, double>(a.rowptr, a.col, a.val, a.x, row, valid, g);
+    const cd s = csr_row27<G, double>(a.rowptr, a.col, a.val, a.x, row, valid, g);
     if (valid && g == 0) {
       const cd bi = a.b[row];
       const cd ri(bi.re - s.re, bi.im - s.im);

@@ -22,6 +22,7 @@
 // effect only in phase C, so the loop-control values every block reads at the top of a step
 // are stable. Converged systems drop out of a compacted tile list.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -221,7 +222,7 @@ __device__ void phaseA_fp64(const KParams& P, int t, double* sh) {
   for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
     const int64_t row = base + gid;
     const bool valid = row < T.row1;
-    const cd s = csr_row<G64, double>(Y.rowptr, Y.col, Y.val, src, row, valid, g);
+    const cd s = csr_row27<G64, double>(Y.rowptr, Y.col, Y.val, src, row, valid, g);
     if (valid && g == 0) {
       Y.q[row] = s;
       const cd pi = src[row];
@@ -254,17 +255,35 @@ __device__ void phaseB_fp64(const KParams& P, int t, double* sh) {
   if (!vload(&S->act)) return;
   const KSys Y = P.sys[T.sys];
   const cd al = S->alpha;
+  const cd mal(-al.re, -al.im);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-    const cd pi = Y.p[i], qi = Y.q[i];
-    cd xi = Y.x[i], ri = Y.r[i];
-    cfma(xi, al, pi);
-    cfma(ri, cd(-al.re, -al.im), qi);
-    Y.x[i] = xi;
-    Y.r[i] = ri;
-    v[0] += ri.re * ri.re - ri.im * ri.im;
-    v[1] += 2.0 * ri.re * ri.im;
-    v[2] += ri.re * ri.re + ri.im * ri.im;
+  constexpr int U = 4;  // rows per thread per pass: all loads issued before the arithmetic
+  for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
+    cd pv[U], qv[U], xv[U], rv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBlock;
+      if (i < T.row1) {
+        pv[u] = Y.p[i];
+        qv[u] = Y.q[i];
+        xv[u] = Y.x[i];
+        rv[u] = Y.r[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBlock;
+      if (i < T.row1) {
+        cfma(xv[u], al, pv[u]);
+        cfma(rv[u], mal, qv[u]);
+        Y.x[i] = xv[u];
+        Y.r[i] = rv[u];
+        const cd ri = rv[u];
+        v[0] += ri.re * ri.re - ri.im * ri.im;
+        v[1] += 2.0 * ri.re * ri.im;
+        v[2] += ri.re * ri.re + ri.im * ri.im;
+      }
+    }
   }
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
@@ -293,10 +312,25 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
   const KSys Y = P.sys[T.sys];
   if (vload(&S->cmode) == C_PUPDATE) {
     const cd be = S->beta;
-    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-      cd pn = Y.r[i];
-      cfma(pn, be, Y.p[i]);
-      Y.p[i] = pn;
+    constexpr int U = 4;
+    for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
+      cd rv[U], pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * kBlock;
+        if (i < T.row1) {
+          rv[u] = Y.r[i];
+          pv[u] = Y.p[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * kBlock;
+        if (i < T.row1) {
+          cfma(rv[u], be, pv[u]);
+          Y.p[i] = rv[u];
+        }
+      }
     }
     return;
   }
@@ -306,7 +340,7 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
   for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
     const int64_t row = base + gid;
     const bool valid = row < T.row1;
-    const cd s = csr_row<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
+    const cd s = csr_row27<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
     if (valid && g == 0) {
       const cd bi = Y.b[row];
       const cd ri(bi.re - s.re, bi.im - s.im);
@@ -351,7 +385,7 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
     for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
       const int64_t row = base + gid;
       const bool valid = row < T.row1;
-      const cd s = csr_row<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
+      const cd s = csr_row27<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
       if (valid && g == 0) {
         const cd bi = Y.b[row];
         const cd ri(bi.re - s.re, bi.im - s.im);
@@ -383,7 +417,7 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
   for (int64_t base = T.row0; base < T.row1; base += kBlock / G32) {
     const int64_t row = base + gid;
     const bool valid = row < T.row1;
-    const cf s = csr_row<G32, float>(Y.rowptr, Y.col, Y.val32, src, row, valid, g);
+    const cf s = csr_row27<G32, float>(Y.rowptr, Y.col, Y.val32, src, row, valid, g);
     if (valid && g == 0) {
       Y.q32[row] = s;
       const cf pi = src[row];
@@ -448,17 +482,35 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
   }
   const cd al = S->alpha;
   const cf a32((float)al.re, (float)al.im);
+  const cf ma32(-a32.re, -a32.im);
   float acc[3] = {0.f, 0.f, 0.f};
-  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-    const cf pi = Y.p32[i], qi = Y.q32[i];
-    cf xi = Y.x32[i], ri = Y.r32[i];
-    cfma(xi, a32, pi);
-    cfma(ri, cf(-a32.re, -a32.im), qi);
-    Y.x32[i] = xi;
-    Y.r32[i] = ri;
-    acc[0] += ri.re * ri.re - ri.im * ri.im;
-    acc[1] += 2.f * ri.re * ri.im;
-    acc[2] += ri.re * ri.re + ri.im * ri.im;
+  constexpr int U = 4;
+  for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
+    cf pv[U], qv[U], xv[U], rv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBlock;
+      if (i < T.row1) {
+        pv[u] = Y.p32[i];
+        qv[u] = Y.q32[i];
+        xv[u] = Y.x32[i];
+        rv[u] = Y.r32[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBlock;
+      if (i < T.row1) {
+        cfma(xv[u], a32, pv[u]);
+        cfma(rv[u], ma32, qv[u]);
+        Y.x32[i] = xv[u];
+        Y.r32[i] = rv[u];
+        const cf ri = rv[u];
+        acc[0] += ri.re * ri.re - ri.im * ri.im;
+        acc[1] += 2.f * ri.re * ri.im;
+        acc[2] += ri.re * ri.re + ri.im * ri.im;
+      }
+    }
   }
   v[0] = acc[0];
   v[1] = acc[1];
@@ -499,10 +551,25 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
   if (vload(&S->cmode) == C_PUPDATE) {
     const cd be = S->beta;
     const cf b32((float)be.re, (float)be.im);
-    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-      cf pn = Y.r32[i];
-      cfma(pn, b32, Y.p32[i]);
-      Y.p32[i] = pn;
+    constexpr int U = 4;
+    for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
+      cf rv[U], pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * kBlock;
+        if (i < T.row1) {
+          rv[u] = Y.r32[i];
+          pv[u] = Y.p32[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * kBlock;
+        if (i < T.row1) {
+          cfma(rv[u], b32, pv[u]);
+          Y.p32[i] = rv[u];
+        }
+      }
     }
     return;
   }
@@ -518,8 +585,8 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
   if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) S->mode = MODE_RESID;
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(kBlock, 2) cocg_persistent(KParams P) {
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
   __shared__ double sh[4 * (kBlock / 32)];
   __shared__ int sh_int[kBlock / 32];
   const unsigned nb = gridDim.x;
@@ -576,11 +643,17 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   int coop = 0;
   HELM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return set_error(HELM_ERR_CUDA, "device does not support cooperative launch");
-  auto kern = mixed ? cocg_persistent<true> : cocg_persistent<false>;
+  // Two register budgets: one block per SM (255 registers, no spills, deep per-thread ILP) or
+  // two (128 registers). HELM_PERSIST_BLOCKS_PER_SM=2 selects the second (tuning knob).
+  const char* env = getenv("HELM_PERSIST_BLOCKS_PER_SM");
+  const int want = (env && atoi(env) == 2) ? 2 : 1;
+  void (*kern)(KParams) = nullptr;
+  if (want == 2) kern = mixed ? cocg_persistent<true, 2> : cocg_persistent<false, 2>;
+  else kern = mixed ? cocg_persistent<true, 1> : cocg_persistent<false, 1>;
   int per_sm = 0;
   HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return set_error(HELM_ERR_CUDA, "persistent kernel cannot be resident");
-  per_sm = std::min(per_sm, 2);
+  per_sm = std::min(per_sm, want);
   const int nblocks = nsm * per_sm;
 
   // tiles: about nblocks tiles for a system that fills the GPU, 256-row multiples

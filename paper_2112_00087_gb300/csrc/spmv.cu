@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(const int32_t* __restrict_
   for (int64_t base = (int64_t)blockIdx.x * RPB; base < n; base += (int64_t)gridDim.x * RPB) {
     const int64_t row = base + gid;
     const bool valid = row < n;
-    cplx<T> s = csr_row<G, T>(rowptr, col, val, x, row, valid, g);
+    cplx<T> s = csr_row27<G, T>(rowptr, col, val, x, row, valid, g);
     if (valid && g == 0) y[row] = s;
   }
 }
