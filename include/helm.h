@@ -148,6 +148,23 @@ helm_status helm_spmv(const helm_matrix* A, const void* x, void* y, void* stream
 helm_status helm_reduce(int32_t op, int64_t n, const double* x, const double* y, double* out,
                         void* stream);
 
+/* The reduction of helm_reduce without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc while they run -- e.g. an
+ * application that reserves all device memory for its own pool at start-up, or a latency-bound
+ * loop that cannot afford the implicit device synchronisation of cudaMalloc / cudaFree. The
+ * caller still passes x, y (dev) and out (host, double[2]); the partial sums go to a static
+ * device array of the library (64 KiB per device, kept until the process exits).
+ *   - n may be at most 16,777,216 (4096 partial sums of 4096 elements); larger n returns
+ *     HELM_ERR_ARG with a message naming the limit.
+ *   - The first call on a device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the array and overwrites what it uses; calls that overlap on the GPU
+ *     (concurrent streams, threads) race and must be serialised by the caller.
+ * Results agree with helm_reduce to rounding (the partial sums are grouped differently);
+ * repeated calls with the same input are bitwise identical. Synchronises `stream`. */
+helm_status helm_reduce_noalloc(int32_t op, int64_t n, const double* x, const double* y,
+                                double* out, void* stream);
+
 /* Frequency response: solve the system of every frequency freqs_hz[0..nfreq) (host) on the
  * context's lattice. p_out (dev, complex128 [nfreq][n]) receives the pressure (the best
  * iterate if not converged); stats (host, [nfreq]) the per-frequency statistics. COCG systems

@@ -246,6 +246,16 @@ helm_status helm_reduce(int32_t op, int64_t n, const double* x, const double* y,
   return reduce_c128(op, n, (const cd*)x, (const cd*)y, out, (cudaStream_t)stream);
 }
 
+helm_status helm_reduce_noalloc(int32_t op, int64_t n, const double* x, const double* y, double* out, void* stream) {
+  if (op < 0 || op > 2 || n < 0 || !out || (n > 0 && !x) || (n > 0 && op != 2 && !y))
+    return set_error(HELM_ERR_ARG, "helm_reduce_noalloc: bad argument");
+  if (n == 0) {
+    out[0] = out[1] = 0.0;
+    return HELM_OK;
+  }
+  return reduce_c128_noalloc(op, n, (const cd*)x, (const cd*)y, out, (cudaStream_t)stream);
+}
+
 helm_status helm_solve(helm_ctx* c, const double* freqs_hz, int32_t nfreq, const helm_solve_opts* opts,
                        double* p_out, helm_solve_stats* stats) {
   if (!c || !freqs_hz || !p_out || !stats || nfreq < 0) return set_error(HELM_ERR_ARG, "helm_solve: bad argument");

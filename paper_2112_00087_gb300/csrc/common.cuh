@@ -118,6 +118,7 @@ helm_status spmv_c128(const int32_t* rowptr, const int32_t* col, const cd* val, 
 helm_status spmv_c64(const int32_t* rowptr, const int32_t* col, const cf* val, const cf* x, cf* y,
                      int64_t n, cudaStream_t s);
 helm_status reduce_c128(int op, int64_t n, const cd* x, const cd* y, double* out_host, cudaStream_t s);
+helm_status reduce_c128_noalloc(int op, int64_t n, const cd* x, const cd* y, double* out_host, cudaStream_t s);
 
 // krylov_cocg.cu
 struct BatchSystem {

@@ -1,6 +1,8 @@
 // Standalone SpMV (paper Sec. 4: CSR storage; SpMV "the most time consuming operation") and
 // deterministic FP64 reductions (dot products / norms of the Krylov methods).
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "kernels.cuh"
 
@@ -109,6 +111,66 @@ helm_status reduce_c128(int op, int64_t n, const cd* x, const cd* y, double* out
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(buf);
   if (e != cudaSuccess) return cuda_error(e, "reduce");
+  if (op == 2) {
+    out_host[0] = sqrt(out_host[0]);
+    out_host[1] = 0.0;
+  }
+  return HELM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Reduction without allocation. The partial sums live in a file-scope device array instead of
+// a cudaMalloc'd buffer, for callers that must not allocate device memory while they run.
+// Block b sums the fixed chunk [b*kNoAllocChunk, (b+1)*kNoAllocChunk), so n is limited to
+// kNoAllocMaxParts * kNoAllocChunk elements.
+// ---------------------------------------------------------------------------------------------
+constexpr int kNoAllocMaxParts = 4096;
+constexpr int64_t kNoAllocChunk = 4096;
+constexpr int64_t kNoAllocMaxN = (int64_t)kNoAllocMaxParts * kNoAllocChunk;  // 16,777,216
+
+// 2 doubles per partial + 2 for the result: 64 KiB + 16 B, held by every device that loads the
+// library until the process exits. Shared by all calls: every call overwrites the entries it
+// uses before reading them, so nothing needs clearing; calls that overlap on the GPU race.
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxParts + 2];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};  // device address of g_noalloc_scratch, per device
+}  // namespace
+
+// Device address of the scratch array on the current device; looked up once per device (the
+// host-side symbol is only a stand-in and must never be passed to a kernel).
+static helm_status noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "helm_reduce_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 256) return set_error(HELM_ERR_ARG, "helm_reduce_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "helm_reduce_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return HELM_OK;
+}
+
+helm_status reduce_c128_noalloc(int op, int64_t n, const cd* x, const cd* y, double* out_host, cudaStream_t s) {
+  if (n > kNoAllocMaxN)
+    return set_error(HELM_ERR_ARG, "helm_reduce_noalloc: n = " + std::to_string(n) + " exceeds the maximum " +
+                                       std::to_string(kNoAllocMaxN) + " of its static scratch");
+  double* buf = nullptr;
+  helm_status st = noalloc_scratch(&buf);
+  if (st != HELM_OK) return st;
+  const int nparts = (int)((n + kNoAllocChunk - 1) / kNoAllocChunk);
+  reduce_stage1<<<nparts, kBlock, 0, s>>>(op, x, y, n, kNoAllocChunk, buf);
+  reduce_stage2<<<1, kBlock, 0, s>>>(buf, nparts, buf + 2 * kNoAllocMaxParts);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_host, buf + 2 * kNoAllocMaxParts, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "helm_reduce_noalloc");
   if (op == 2) {
     out_host[0] = sqrt(out_host[0]);
     out_host[1] = 0.0;

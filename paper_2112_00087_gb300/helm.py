@@ -27,7 +27,8 @@ HELM_PRECOND_NONE, HELM_PRECOND_RAS = 0, 1
 # Symbols declared in include/helm.h (tests check the library exports all of them).
 EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary", "helm_sizes",
             "helm_assemble", "helm_matrix_free", "helm_matrix_csr", "helm_spmv", "helm_reduce",
-            "helm_solve", "helm_solve_batch", "helm_adjoint_grad", "helm_adjoint_seed", "helm_last_profile"]
+            "helm_solve", "helm_solve_batch", "helm_adjoint_grad", "helm_adjoint_seed", "helm_last_profile",
+            "helm_reduce_noalloc"]
 
 
 class HelmError(RuntimeError):
@@ -86,6 +87,7 @@ def _load():
         "helm_matrix_csr": (i32, [vp, P(i64), P(i64), P(i32), P(vp), P(vp), P(vp)]),
         "helm_spmv": (i32, [vp, vp, vp, vp]),
         "helm_reduce": (i32, [i32, i64, vp, vp, P(d), vp]),
+        "helm_reduce_noalloc": (i32, [i32, i64, vp, vp, P(d), vp]),
         "helm_solve": (i32, [vp, P(d), i32, P(SolveOpts), vp, P(SolveStats)]),
         "helm_solve_batch": (i32, [P(vp), P(d), i32, P(SolveOpts), P(vp), P(SolveStats)]),
         "helm_adjoint_grad": (i32, [vp, P(d), i32, P(SolveOpts), vp, vp, vp, vp, P(d)]),
@@ -268,6 +270,14 @@ def helm_reduce(op: int, x: torch.Tensor, y: Optional[torch.Tensor] = None, stre
     assert x.dtype == torch.complex128 and (y is None or (y.dtype == torch.complex128 and y.numel() == x.numel()))
     out = (ctypes.c_double * 2)()
     _check(LIB.helm_reduce(op, x.numel(), _ptr(x), _ptr(y), out, _stream(stream)))
+    return complex(out[0], out[1])
+
+
+def helm_reduce_noalloc(op: int, x: torch.Tensor, y: Optional[torch.Tensor] = None, stream=None) -> complex:
+    """helm_reduce without device allocation (static library scratch; n <= 16,777,216)."""
+    assert x.dtype == torch.complex128 and (y is None or (y.dtype == torch.complex128 and y.numel() == x.numel()))
+    out = (ctypes.c_double * 2)()
+    _check(LIB.helm_reduce_noalloc(op, x.numel(), _ptr(x), _ptr(y), out, _stream(stream)))
     return complex(out[0], out[1])
 
 
