@@ -53,18 +53,25 @@ def spmv_bytes(n, nnz, vb):
     return nnz * (vb + 4) + (n + 1) * 4 + 2 * vb * n
 
 
+def dia_spmv_bytes(n, vb):
+    """Slot-major 27-point SpMV: 27 n stored values + x read once + y written once."""
+    return 27 * n * vb + 2 * vb * n
+
+
 def cocg_fp64_bytes(n, nnz, st):
     it, chk = st["iterations"], st["restarts"] + 1
-    per_it = spmv_bytes(n, nnz, 16) + 96 * n + 48 * n      # SpMV, x/r update, p update
-    check = spmv_bytes(n, nnz, 16) + 32 * n                 # b read, r written
-    return it * per_it + chk * check + 48 * n               # + init (b read, x and r written)
+    per_it = dia_spmv_bytes(n, 16) + 96 * n + 48 * n      # SpMV, x/r update, p update
+    check = dia_spmv_bytes(n, 16) + 32 * n                # b read, r written
+    return it * per_it + chk * check + 48 * n             # + init (b read, x and r written)
 
 
 def cocg_mixed_bytes(n, nnz, st):
-    it, outer = st["iterations"], st["outer"]
-    inner = spmv_bytes(n, nnz, 8) + 48 * n + 24 * n         # c64 SpMV, x/r update, p update
-    resid = spmv_bytes(n, nnz, 16) + 32 * n                 # FP64 true residual
-    return it * inner + (outer + 1) * resid + outer * (32 * n + 40 * n) + 48 * n
+    it32, outer = st["iterations_c64"], abs(st["outer"])
+    it64 = st["iterations"] - it32                        # FP64 COCG steps after a fallback
+    inner = dia_spmv_bytes(n, 8) + 48 * n + 24 * n        # c64 SpMV, x/r update, p update
+    resid = dia_spmv_bytes(n, 16) + 32 * n                # FP64 true residual
+    fp64 = dia_spmv_bytes(n, 16) + 96 * n + 48 * n
+    return it32 * inner + it64 * fp64 + (outer + 1) * resid + outer * (32 * n + 40 * n) + 48 * n
 
 
 # ---------------------------------------------------------------------------------------------
@@ -144,7 +151,7 @@ def build_sweep(nfreq, helm, torch, workload="sweep256"):
 
 
 def mixed_opts(helm, maxit=400000):
-    return helm.make_opts("cocg", tol=TOL, maxit=maxit, mixed=True, inner_tol=1e-4, inner_maxit=60000, max_outer=40)
+    return helm.make_opts("cocg", tol=TOL, maxit=maxit, mixed=True, inner_tol=1e-4, inner_maxit=600, max_outer=40)
 
 
 def fp64_opts(helm, maxit=400000):
@@ -179,8 +186,12 @@ def spmv_roofline(helm, torch, peak_gbs):
                      torch.from_numpy(pr.p_dir).cuda())
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {}
-    for name, prec, dt, vb in (("c128", helm.HELM_C128, torch.complex128, 16), ("c64", helm.HELM_C64, torch.complex64, 8)):
-        A = helm.helm_assemble(ctx, 250.0, prec, with_rhs=False)
+    cases = (("csr_c128", helm.HELM_C128, helm.HELM_FMT_CSR, torch.complex128, 16),
+             ("csr_c64", helm.HELM_C64, helm.HELM_FMT_CSR, torch.complex64, 8),
+             ("dia27_c128", helm.HELM_C128, helm.HELM_FMT_DIA27, torch.complex128, 16),
+             ("dia27_c64", helm.HELM_C64, helm.HELM_FMT_DIA27, torch.complex64, 8))
+    for name, prec, fmt, dt, vb in cases:
+        A = helm.helm_assemble(ctx, 250.0, prec, with_rhs=False, fmt=fmt)
         x = torch.randn(ctx.n, dtype=dt, device="cuda")
         y = torch.empty_like(x)
         for _ in range(3):
@@ -195,7 +206,9 @@ def spmv_roofline(helm, torch, peak_gbs):
             e1.record(s)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1000.0)
-        b = spmv_bytes(ctx.n, ctx.nnz, vb)
+        # CSR: values + columns + rowptr + x + y; DIA27: the 27 n stored values (padding
+        # included, no columns) + x + y
+        b = spmv_bytes(ctx.n, ctx.nnz, vb) if fmt == helm.HELM_FMT_CSR else 27 * ctx.n * vb + 2 * vb * ctx.n
         best, med = min(times), statistics.median(times)
         out[name] = {"n": ctx.n, "nnz": ctx.nnz, "bytes": b, "best_ms": best * 1e3, "median_ms": med * 1e3,
                      "gbs_best": b / best / 1e9, "gbs_median": b / med / 1e9, "frac_median": b / med / 1e9 / peak_gbs}
@@ -288,9 +301,10 @@ def run_gpu(args):
                             (sum(c.nnz * 32 for c in ctxs) / 1e9),
                       "parallelism": "replicas" if world > 1 else "1 GPU"},
            "converged": "%d/%d" % (n_ok, nsys),
-           "iterations": {"inner_total": int(sum(s["iterations"] for s in stats)),
+           "iterations": {"total": int(sum(s["iterations"] for s in stats)),
+                          "c64_total": int(sum(s["iterations_c64"] for s in stats)),
                           "max": int(max(s["iterations"] for s in stats)),
-                          "outer_max": int(max(s["outer"] for s in stats)),
+                          "fell_back_to_fp64": int(sum(1 for s in stats if s["outer"] < 0)),
                           "relres_max": max(s["relres"] for s in stats)},
            "phases_ms": {"assemble": prof["assemble_ms"], "solve": prof["solve_ms"]},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
@@ -301,8 +315,9 @@ def run_gpu(args):
 
     if args.verbose and rank == 0:
         for c, f, st_ in zip(ctxs, freqs, stats):
-            print("sys f=%7.2f n=%8d its=%6d outer=%3d restarts=%3d status=%d relres=%.2e" %
-                  (f, c.n, st_["iterations"], st_["outer"], st_["restarts"], st_["status"], st_["relres"]),
+            print("sys f=%7.2f n=%8d its=%6d c64=%6d outer=%3d restarts=%3d status=%d relres=%.2e" %
+                  (f, c.n, st_["iterations"], st_["iterations_c64"], st_["outer"], st_["restarts"], st_["status"],
+                   st_["relres"]),
                   file=sys.stderr, flush=True)
     if rank == 0 and not args.quick:
         # plain FP64 on the same sweep: batched (one launch) and one frequency at a time

@@ -61,6 +61,7 @@ typedef enum {
 } helm_status;
 
 enum { HELM_C128 = 0, HELM_C64 = 1 };                 /* matrix value precision */
+enum { HELM_FMT_CSR = 0, HELM_FMT_DIA27 = 1 };         /* matrix layout (see helm_assemble) */
 enum { HELM_SOLVER_GMRES = 0, HELM_SOLVER_COCG = 1 }; /* Krylov method */
 enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1 }; /* right preconditioner (GMRES only) */
 
@@ -73,7 +74,10 @@ typedef struct {
   int32_t precond;      /* HELM_PRECOND_NONE or HELM_PRECOND_RAS (GMRES only) */
   int32_t ras_parts[3]; /* Schwarz blocks along x, y, z */
   int32_t ras_overlap;  /* lattice layers of overlap */
-  int32_t mixed;        /* 1: FP64 iterative refinement around a complex64 inner COCG (COCG only) */
+  int32_t mixed;        /* 1: FP64 iterative refinement around a complex64 inner COCG (COCG only);
+                           a system whose refinement step fails to halve the FP64 residual
+                           continues as FP64 COCG from its current iterate (stats.outer < 0 marks
+                           such a fallback: -outer refinement steps were taken before it) */
   double inner_tol;     /* mixed: inner relative residual reduction per refinement step */
   int32_t inner_maxit;  /* mixed: inner steps per refinement step */
   int32_t max_outer;    /* mixed: refinement steps before HELM_NOT_CONVERGED */
@@ -86,6 +90,8 @@ typedef struct {
   int32_t outer;        /* mixed: refinement steps taken */
   double relres;        /* true FP64 ||b - A p|| / ||b|| at exit */
   double bnorm;         /* ||b||_2 */
+  int32_t iterations_c64; /* mixed: the complex64 inner steps among `iterations` */
+  int32_t pad;
 } helm_solve_stats;
 
 typedef struct {
@@ -123,22 +129,31 @@ helm_status helm_set_boundary(helm_ctx* ctx, const double* beta_face, const int3
 helm_status helm_sizes(const helm_ctx* ctx, int64_t* n_nodes, int64_t* nnz, int64_t* n_bface,
                        int32_t* n_dir);
 
-/* Assemble the eliminated system matrix at frequency freq_hz (paper Sec. 3.2 Helmholtz eq.,
- * Sec. 4 CSR storage) in `precision` (HELM_C128 or HELM_C64: complex64 values rounded from the
- * complex128 ones). If b_out (dev, complex128 [n]) is not NULL the lifted right-hand side
- * b_F = -A_FD p_D, b_D = p_D is written there. *A_out is owned by the caller's handle until
- * helm_matrix_free. */
-helm_status helm_assemble(helm_ctx* ctx, double freq_hz, int32_t precision, helm_matrix** A_out,
-                          double* b_out);
+/* Assemble the eliminated system matrix at frequency freq_hz (paper Sec. 3.2 Helmholtz eq.)
+ * in `precision` (HELM_C128, or HELM_C64: complex64 values rounded from the complex128 ones)
+ * and `format`:
+ *   HELM_FMT_CSR   -- compressed sparse rows (paper Sec. 4), the context's 27-point pattern;
+ *   HELM_FMT_DIA27 -- slot-major 27-point layout: val[k * n + row], k = (di+1) + 3 (dj+1) +
+ *                     9 (dl+1) for the neighbour row + di + (nx+1) (dj + (ny+1) dl); slots whose
+ *                     neighbour is outside the lattice hold zero. Same values as the CSR form.
+ * If b_out (dev, complex128 [n]) is not NULL the lifted right-hand side b_F = -A_FD p_D,
+ * b_D = p_D is written there. *A_out is owned by the caller's handle until helm_matrix_free and
+ * must be freed before its context. */
+helm_status helm_assemble(helm_ctx* ctx, double freq_hz, int32_t precision, int32_t format,
+                          helm_matrix** A_out, double* b_out);
 void helm_matrix_free(helm_matrix* A);
 
-/* Read-only views of an assembled matrix: rowptr (dev int32 [n+1]), col (dev int32 [nnz]),
- * val (dev complex [nnz], complex128 or complex64 per precision). Any pointer may be NULL. */
+/* Read-only views of a CSR matrix: rowptr (dev int32 [n+1]), col (dev int32 [nnz]), val (dev
+ * complex [nnz], complex128 or complex64 per precision). Any pointer may be NULL.
+ * HELM_ERR_ARG for a DIA27 matrix. */
 helm_status helm_matrix_csr(const helm_matrix* A, int64_t* n, int64_t* nnz, int32_t* precision,
                             const int32_t** rowptr, const int32_t** col, const void** val);
 
-/* y = A x (paper Sec. 4: "the most time consuming operation"). x, y (dev) complex [n] in the
- * matrix precision (complex64 matrices accumulate in FP32), must not overlap. Ordered on
+/* Read-only view of a DIA27 matrix: val (dev complex [27 n], layout above). HELM_ERR_ARG for CSR. */
+helm_status helm_matrix_dia27(const helm_matrix* A, int64_t* n, int32_t* precision, const void** val);
+
+/* y = A x (paper Sec. 4: "the most time consuming operation") for either layout. x, y (dev)
+ * complex [n] in the matrix precision (complex64 matrices accumulate in FP32), must not overlap. Ordered on
  * `stream` (cudaStream_t; NULL = the context stream of the matrix). */
 helm_status helm_spmv(const helm_matrix* A, const void* x, void* y, void* stream);
 

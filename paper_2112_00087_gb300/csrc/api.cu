@@ -182,23 +182,28 @@ helm_status helm_sizes(const helm_ctx* c, int64_t* n_nodes, int64_t* nnz, int64_
   return HELM_OK;
 }
 
-helm_status helm_assemble(helm_ctx* c, double freq_hz, int32_t precision, helm_matrix** A_out, double* b_out) {
+helm_status helm_assemble(helm_ctx* c, double freq_hz, int32_t precision, int32_t format, helm_matrix** A_out,
+                          double* b_out) {
   if (!c || !A_out) return set_error(HELM_ERR_ARG, "helm_assemble: null argument");
   *A_out = nullptr;
   if (!(freq_hz >= 0) || !std::isfinite(freq_hz)) return set_error(HELM_ERR_ARG, "helm_assemble: bad frequency");
   if (precision != HELM_C128 && precision != HELM_C64) return set_error(HELM_ERR_ARG, "helm_assemble: bad precision");
+  if (format != HELM_FMT_CSR && format != HELM_FMT_DIA27) return set_error(HELM_ERR_ARG, "helm_assemble: bad format");
   helm_matrix* A = new (std::nothrow) helm_matrix;
   if (!A) return set_error(HELM_ERR_OOM, "helm_assemble: host allocation failed");
   memset(A, 0, sizeof(*A));
   A->ctx = c;
   A->n = c->n;
-  A->nnz = c->nnz;
+  A->nnz = format == HELM_FMT_DIA27 ? 27 * c->n : c->nnz;
   A->precision = precision;
+  A->format = format;
   A->freq = freq_hz;
-  helm_status st = dev_alloc(&A->val, c->nnz);
-  if (st == HELM_OK && precision == HELM_C64) st = dev_alloc(&A->val32, c->nnz);
-  if (st == HELM_OK) st = assemble_values(c, freq_hz, A->val, (cd*)b_out, c->stream);
-  if (st == HELM_OK && precision == HELM_C64) st = cast_values(A->val, A->val32, c->nnz, c->stream);
+  helm_status st = dev_alloc(&A->val, A->nnz);
+  if (st == HELM_OK && precision == HELM_C64) st = dev_alloc(&A->val32, A->nnz);
+  if (st == HELM_OK && format == HELM_FMT_DIA27) st = dev_alloc(&A->cflag, c->n);
+  if (st == HELM_OK)
+    st = assemble_values(c, freq_hz, A->val, (cd*)b_out, c->stream, true, format == HELM_FMT_DIA27, A->cflag);
+  if (st == HELM_OK && precision == HELM_C64) st = cast_values(A->val, A->val32, A->nnz, c->stream);
   if (st != HELM_OK) {
     helm_matrix_free(A);
     return st;
@@ -212,12 +217,14 @@ void helm_matrix_free(helm_matrix* A) {
   cudaStreamSynchronize(A->ctx ? A->ctx->stream : 0);
   cudaFree(A->val);
   cudaFree(A->val32);
+  cudaFree(A->cflag);
   delete A;
 }
 
 helm_status helm_matrix_csr(const helm_matrix* A, int64_t* n, int64_t* nnz, int32_t* precision,
                             const int32_t** rowptr, const int32_t** col, const void** val) {
   if (!A) return set_error(HELM_ERR_ARG, "helm_matrix_csr: null matrix");
+  if (A->format != HELM_FMT_CSR) return set_error(HELM_ERR_ARG, "helm_matrix_csr: matrix is not CSR");
   if (n) *n = A->n;
   if (nnz) *nnz = A->nnz;
   if (precision) *precision = A->precision;
@@ -227,10 +234,24 @@ helm_status helm_matrix_csr(const helm_matrix* A, int64_t* n, int64_t* nnz, int3
   return HELM_OK;
 }
 
+helm_status helm_matrix_dia27(const helm_matrix* A, int64_t* n, int32_t* precision, const void** val) {
+  if (!A) return set_error(HELM_ERR_ARG, "helm_matrix_dia27: null matrix");
+  if (A->format != HELM_FMT_DIA27) return set_error(HELM_ERR_ARG, "helm_matrix_dia27: matrix is not DIA27");
+  if (n) *n = A->n;
+  if (precision) *precision = A->precision;
+  if (val) *val = A->precision == HELM_C64 ? (const void*)A->val32 : (const void*)A->val;
+  return HELM_OK;
+}
+
 helm_status helm_spmv(const helm_matrix* A, const void* x, void* y, void* stream) {
   if (!A || !x || !y) return set_error(HELM_ERR_ARG, "helm_spmv: null argument");
   if (x == y) return set_error(HELM_ERR_ARG, "helm_spmv: x and y must not overlap");
   cudaStream_t s = stream ? (cudaStream_t)stream : A->ctx->stream;
+  if (A->format == HELM_FMT_DIA27) {
+    const int64_t Nx = A->ctx->mesh.nx + 1, NxNy = Nx * (A->ctx->mesh.ny + 1);
+    if (A->precision == HELM_C64) return spmv_dia_c64(A->val32, A->cflag, (const cf*)x, (cf*)y, A->n, Nx, NxNy, s);
+    return spmv_dia_c128(A->val, A->cflag, (const cd*)x, (cd*)y, A->n, Nx, NxNy, s);
+  }
   if (A->precision == HELM_C64)
     return spmv_c64(A->ctx->rowptr, A->ctx->col, A->val32, (const cf*)x, (cf*)y, A->n, s);
   return spmv_c128(A->ctx->rowptr, A->ctx->col, A->val, (const cd*)x, (cd*)y, A->n, s);

@@ -88,10 +88,13 @@ __device__ inline void side_term(const cd* __restrict__ beta, int64_t base, int 
     }
 }
 
+// DIA = false: CSR values at rowptr[r]..; DIA = true: slot-major values val[k * n + r] with
+// k = (di+1) + 3 (dj+1) + 9 (dl+1) and zeros for neighbours outside the lattice.
+template <bool DIA>
 __global__ void values_kernel(Lattice L, double k2, double krc, const int32_t* __restrict__ rowptr,
                               const cd* __restrict__ beta, const uint8_t* __restrict__ is_dir,
                               const cd* __restrict__ pdir, cd* __restrict__ val, cd* __restrict__ b,
-                              int64_t n) {
+                              uint8_t* __restrict__ cflag, int64_t n) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
   int i = (int)(r % L.Nx);
@@ -102,7 +105,10 @@ __global__ void values_kernel(Lattice L, double k2, double krc, const int32_t* _
                 o_zp = o_zm + (int64_t)L.nx * L.ny;
   const bool rowD = is_dir != nullptr && is_dir[r] != 0;
   cd bsum(0.0, 0.0);
-  int64_t k = rowptr[r];
+  bool row_complex = false;
+  int64_t k = DIA ? 0 : rowptr[r];
+  if (DIA)
+    for (int s = 0; s < 27; ++s) val[(int64_t)s * n + r] = cd(0.0, 0.0);
   for (int dl = -1; dl <= 1; ++dl) {
     if (l + dl < 0 || l + dl >= L.Nz) continue;
     double kz, mz;
@@ -113,6 +119,7 @@ __global__ void values_kernel(Lattice L, double k2, double krc, const int32_t* _
       entries1(j, dj, L.ny, L.hy, ky, my);
       for (int di = -1; di <= 1; ++di) {
         if (i + di < 0 || i + di >= L.Nx) continue;
+        if (DIA) k = (int64_t)((di + 1) + 3 * (dj + 1) + 9 * (dl + 1)) * n + r;
         double kx, mx;
         entries1(i, di, L.nx, L.hx, kx, mx);
         const int64_t c = r + di + (int64_t)L.Nx * (dj + (int64_t)L.Ny * dl);
@@ -138,11 +145,14 @@ __global__ void values_kernel(Lattice L, double k2, double krc, const int32_t* _
           bsum.im += a.re * pc.im + a.im * pc.re;
           a = cd(0.0, 0.0);
         }
-        val[k++] = a;
+        val[k] = a;
+        row_complex |= (a.im != 0.0);
+        if (!DIA) ++k;
       }
     }
   }
   if (b != nullptr) b[r] = rowD ? pdir[r] : cd(-bsum.re, -bsum.im);
+  if (cflag != nullptr) cflag[r] = row_complex ? 1 : 0;
 }
 
 __global__ void cast_kernel(const cd* __restrict__ v, cf* __restrict__ v32, int64_t nnz) {
@@ -165,14 +175,15 @@ helm_status build_pattern(helm_ctx* ctx) {
   return HELM_OK;
 }
 
-helm_status assemble_values(const helm_ctx* ctx, double freq, cd* val, cd* b, cudaStream_t s, bool eliminate) {
+helm_status assemble_values(const helm_ctx* ctx, double freq, cd* val, cd* b, cudaStream_t s, bool eliminate,
+                            bool dia, uint8_t* cflag) {
   Lattice L = make_lattice(ctx->mesh);
   const double k = 2.0 * 3.14159265358979323846 * freq / ctx->phys.c;
   const int T = 128;
   int64_t blocks = (ctx->n + T - 1) / T;
-  values_kernel<<<(unsigned)blocks, T, 0, s>>>(L, k * k, k * ctx->phys.rho * ctx->phys.c, ctx->rowptr,
+  (dia ? values_kernel<true> : values_kernel<false>)<<<(unsigned)blocks, T, 0, s>>>(L, k * k, k * ctx->phys.rho * ctx->phys.c, ctx->rowptr,
                                                ctx->beta, eliminate ? ctx->is_dir : nullptr,
-                                               ctx->p_dir_full, val, eliminate ? b : nullptr, ctx->n);
+                                               ctx->p_dir_full, val, eliminate ? b : nullptr, cflag, ctx->n);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }

@@ -96,20 +96,24 @@ struct helm_ctx {
 
 struct helm_matrix {
   const helm_ctx* ctx;  // pattern owner (must outlive the matrix)
-  int64_t n, nnz;
+  int64_t n, nnz;       // nnz: stored entries (CSR nnz, or 27 n for the slot-major layout)
   int32_t precision;
+  int32_t format;       // HELM_FMT_CSR or HELM_FMT_DIA27
   double freq;
   helm::cd* val;        // complex128 values (always present)
   helm::cf* val32;      // complex64 values (HELM_C64 only)
+  uint8_t* cflag;       // DIA27: 1 for rows with a non-zero imaginary entry
 };
 
 namespace helm {
 
 // assemble.cu
 helm_status build_pattern(helm_ctx* ctx);
-// eliminate = false: the matrix before Dirichlet elimination (b is not written)
+// eliminate = false: the matrix before Dirichlet elimination (b is not written).
+// dia = true: slot-major 27-point layout val[k * n + row] (27 n entries) instead of CSR.
+// cflag (u8 [n], may be null): 1 for rows with a non-zero imaginary entry.
 helm_status assemble_values(const helm_ctx* ctx, double freq, cd* val, cd* b, cudaStream_t s,
-                            bool eliminate = true);
+                            bool eliminate = true, bool dia = false, uint8_t* cflag = nullptr);
 helm_status cast_values(const cd* val, cf* val32, int64_t nnz, cudaStream_t s);
 
 // spmv.cu
@@ -117,6 +121,10 @@ helm_status spmv_c128(const int32_t* rowptr, const int32_t* col, const cd* val, 
                       int64_t n, cudaStream_t s);
 helm_status spmv_c64(const int32_t* rowptr, const int32_t* col, const cf* val, const cf* x, cf* y,
                      int64_t n, cudaStream_t s);
+helm_status spmv_dia_c128(const cd* val, const uint8_t* cflag, const cd* x, cd* y, int64_t n, int64_t Nx,
+                          int64_t NxNy, cudaStream_t s);
+helm_status spmv_dia_c64(const cf* val, const uint8_t* cflag, const cf* x, cf* y, int64_t n, int64_t Nx,
+                         int64_t NxNy, cudaStream_t s);
 helm_status reduce_c128(int op, int64_t n, const cd* x, const cd* y, double* out_host, cudaStream_t s);
 helm_status reduce_c128_noalloc(int op, int64_t n, const cd* x, const cd* y, double* out_host, cudaStream_t s);
 

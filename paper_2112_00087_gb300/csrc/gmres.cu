@@ -536,6 +536,8 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
     st->outer = 0;
     st->relres = hctl->relres;
     st->bnorm = hctl->bnorm;
+    st->iterations_c64 = 0;
+    st->pad = 0;
     result = (helm_status)st->status;
   } else {
     st->status = result;

@@ -110,6 +110,65 @@ __device__ __forceinline__ cplx<T> csr_row27(const int32_t* __restrict__ rowptr,
   return acc;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Slot-major 27-point layout ("DIA-27"): val[k * n + row] holds the entry of `row` for lattice
+// offset k = (di+1) + 3 (dj+1) + 9 (dl+1), column row + di + Nx (dj + Ny dl); entries whose
+// neighbour lies outside the lattice are stored as zero. One thread per row: the value loads
+// and the x gathers of a warp are contiguous, no column indices are read, and no lanes are
+// idle. Gather indices are clamped into [0, n) so that padded slots (value 0) read a valid
+// address; 0 * x adds nothing for finite x, so the clamp never changes a result. A per-row
+// byte flag (set at assembly) marks rows with a non-zero imaginary entry.
+// ---------------------------------------------------------------------------------------------
+// Real-part product of one row: sum_k Re(a_k) x_{c_k}. Three independent accumulation chains
+// per component (one per stencil line dj = -1, 0, 1), so consecutive multiply-adds do not wait
+// on each other. Complex entries occur only next to admittance walls; their imaginary parts are
+// added by dia_row_im in a second pass that only rows flagged at assembly take -- on GB300 the
+// FP64 pipe is the bottleneck, so the common real rows must not issue any imaginary FMA.
+template <typename T>
+__device__ __forceinline__ cplx<T> dia_row_re(const cplx<T>* __restrict__ val, const cplx<T>* x, int64_t n,
+                                              int64_t Nx, int64_t NxNy, int64_t row) {
+  cplx<T> acc[3] = {cplx<T>(T(0), T(0)), cplx<T>(T(0), T(0)), cplx<T>(T(0), T(0))};
+#pragma unroll
+  for (int dl = -1; dl <= 1; ++dl) {
+    T a[9];
+    cplx<T> xv[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {  // all loads of one lattice plane first
+      const int di = q % 3 - 1, dj = q / 3 - 1;
+      const int k = q + 9 * (dl + 1);
+      int64_t c = row + di + Nx * dj + NxNy * dl;
+      c = c < 0 ? 0 : (c >= n ? n - 1 : c);
+      a[q] = ld_stream(val + (int64_t)k * n + row).re;
+      xv[q] = x[c];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      cplx<T>& s = acc[q / 3];
+      s.re = fma(a[q], xv[q].re, s.re);
+      s.im = fma(a[q], xv[q].im, s.im);
+    }
+  }
+  return cplx<T>((acc[0].re + acc[1].re) + acc[2].re, (acc[0].im + acc[1].im) + acc[2].im);
+}
+
+// Imaginary-part product of one row: sum_k i Im(a_k) x_{c_k}.
+template <typename T>
+__device__ __forceinline__ cplx<T> dia_row_im(const cplx<T>* __restrict__ val, const cplx<T>* x, int64_t n,
+                                              int64_t Nx, int64_t NxNy, int64_t row) {
+  cplx<T> acc(T(0), T(0));
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dl = k / 9 - 1;
+    int64_t c = row + di + Nx * dj + NxNy * dl;
+    c = c < 0 ? 0 : (c >= n ? n - 1 : c);
+    const T b = val[(int64_t)k * n + row].im;
+    const cplx<T> xv = x[c];
+    acc.re = fma(-b, xv.im, acc.re);
+    acc.im = fma(b, xv.re, acc.im);
+  }
+  return acc;
+}
+
 // Deterministic block sum of NV doubles per thread (fixed shuffle tree, then warps in order).
 // Every thread gets the result. `sh` must hold NV * (kBlock/32) doubles.
 template <int NV>
@@ -137,7 +196,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
 // ---------------------------------------------------------------------------------------------
 // Bounded grid barrier for cooperative (co-resident) launches. Arrival: fence, then one atomic
 // per block; the last arriver resets the count and bumps the generation. Waiters spin on the
-// generation with an acquire load, give up after kSpinLimit polls or kTimeoutNs nanoseconds,
+// generation with an acquire load (no sleep between polls: one polling thread per block, and a
+// sleep's wake-up granularity would add to every barrier), give up after kSpinLimit polls or
+// kTimeoutNs nanoseconds,
 // record DEV_TIMEOUT in the status word and return false so the kernel can unwind.
 // ---------------------------------------------------------------------------------------------
 struct GridBar {
@@ -148,7 +209,7 @@ struct GridBar {
 };
 
 constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s
-constexpr unsigned kSpinLimit = 200000000u;
+constexpr unsigned kSpinLimit = 1000000000u;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -183,7 +244,6 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();

@@ -11,7 +11,13 @@
 // Mixed precision (FP64 iterative refinement, complex64 inner solve): r = b - A x in FP64,
 // inner COCG on A d = r / ||r|| with complex64 matrix, vectors and SpMV accumulation, stopped at
 // an inner reduction inner_tol, then x += ||r|| d in FP64. The true residual, the refinement
-// update and the convergence test stay FP64; the inner dot products accumulate in FP64.
+// update and the convergence test stay FP64; the inner dot products accumulate in FP64. A system
+// whose refinement step fails to halve the FP64 residual (complex64 COCG stalls on strongly
+// indefinite systems) continues as FP64 COCG from its current iterate in the same launch; an
+// inner solve that did not reduce its own residual contributes no correction.
+//
+// Matrices are stored slot-major (27 values per row, val[k * n + row], columns implicit from
+// the lattice offsets), one thread per row.
 //
 // Every system of the batch (its own lattice, frequency and matrix) is cut into row tiles.
 // One launch runs all systems in lockstep super-steps of three phases (A: SpMV + dot, B: axpys
@@ -33,10 +39,10 @@ namespace {
 
 struct KSys {
   int64_t n;
-  const int32_t* rowptr;
-  const int32_t* col;
-  const cd* val;
-  const cf* val32;
+  int64_t Nx, NxNy;   // lattice strides of the slot-major 27-point layout
+  const cd* val;      // [27][n] complex128
+  const cf* val32;    // [27][n] complex64 (mixed)
+  const uint8_t* cflag;  // [n] 1 for rows with a non-zero imaginary entry
   const cd* b;
   cd* x;
   cd* r;
@@ -49,7 +55,7 @@ struct KSys {
   int tile0, ntiles;
 };
 
-enum : int { MODE_RESID = 0, MODE_INNER = 1 };
+enum : int { MODE_RESID = 0, MODE_INNER = 1, MODE_FP64 = 2 };
 enum : int { C_PUPDATE = 0, C_CHECK = 1, C_XUPDATE = 2 };
 
 struct KState {
@@ -57,15 +63,20 @@ struct KState {
   int amode;     // phase A source: 0 = p, 1 = r (and p := r)
   int cmode;     // phase C action
   int mode;      // mixed: MODE_RESID / MODE_INNER
-  int it;        // Krylov steps (inner steps when mixed)
+  int it;        // Krylov steps (complex64 inner and FP64 steps)
+  int it32;      // complex64 inner steps
   int inner_it;
   int outer;
   int restarts;
   int status;
   int bd;        // breakdown seen
   int pend;      // mixed: finish pending (status in `status`)
+  int to_fp64;   // mixed: switch to FP64 COCG at the end of this step
+  int discard;   // mixed: the inner solve did not reduce its residual; skip its correction
+  int fell_back; // mixed: the system finished in FP64 COCG
+  int reset_x;   // mixed: the fallback restarts from x = 0 (refinement left x worse than zero)
   unsigned arrive;
-  double bnorm, rnorm, relres, est;
+  double bnorm, rnorm, relres, est, prev_rel;
   cd rho, alpha, beta;
 };
 
@@ -95,8 +106,6 @@ struct KParams {
   int max_steps;
 };
 
-constexpr int G64 = 4;  // lanes per row, complex128 SpMV
-constexpr int G32 = 8;  // lanes per row, complex64 SpMV
 
 __device__ __forceinline__ int vload(const int* p) { return *((volatile const int*)p); }
 
@@ -179,6 +188,47 @@ __device__ bool rebuild_list(const KParams& P, int cur, int& seen_fin, int* sh_i
   return true;
 }
 
+// Product of the tile's rows with x in two passes: first(row, s_re, complex_flag) for every
+// row with the real-part product (two rows per thread, so their loads overlap), then, if any
+// row of the tile is flagged complex (block-uniform), fix(row, s_im) for each flagged row with
+// its imaginary-part product. Thread t handles rows row0 + t + m kBlock in both passes, so a
+// thread reads back only what it wrote itself.
+#ifndef HELM_ROWS_PER_THREAD
+#define HELM_ROWS_PER_THREAD 2
+#endif
+#ifndef HELM_VEC_UNROLL
+#define HELM_VEC_UNROLL 4
+#endif
+
+template <typename T, typename F1, typename F2>
+__device__ __forceinline__ void tile_spmv(const cplx<T>* val, const uint8_t* cflag, const cplx<T>* x, int64_t n,
+                                          int64_t Nx, int64_t NxNy, int64_t row0, int64_t row1, F1 first,
+                                          F2 fix) {
+  int has_c = 0;
+  if (HELM_ROWS_PER_THREAD == 2) {
+    for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += 2 * kBlock) {
+      const int64_t r1 = r0 + kBlock < row1 ? r0 + kBlock : r0;  // clamped only in a ragged tail
+      const cplx<T> s0 = dia_row_re<T>(val, x, n, Nx, NxNy, r0);
+      const cplx<T> s1 = dia_row_re<T>(val, x, n, Nx, NxNy, r1);
+      const int c0 = cflag[r0], c1 = cflag[r1];
+      first(r0, s0, c0);
+      if (r1 != r0) first(r1, s1, c1);
+      has_c |= c0 | c1;
+    }
+  } else {
+    for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += kBlock) {
+      const cplx<T> s0 = dia_row_re<T>(val, x, n, Nx, NxNy, r0);
+      const int c0 = cflag[r0];
+      first(r0, s0, c0);
+      has_c |= c0;
+    }
+  }
+  if (__syncthreads_or(has_c)) {
+    for (int64_t row = row0 + threadIdx.x; row < row1; row += kBlock)
+      if (cflag[row]) fix(row, dia_row_im<T>(val, x, n, Nx, NxNy, row));
+  }
+}
+
 // ------------------------------- FP64 COCG phases ---------------------------------------------
 
 __device__ void init_tile(const KParams& P, int t, double* sh, bool mixed) {
@@ -205,6 +255,7 @@ __device__ void init_tile(const KParams& P, int t, double* sh, bool mixed) {
       S->rho = rho;
       S->amode = 1;
       S->mode = MODE_RESID;
+      S->prev_rel = 1.0;
       if (S->bnorm == 0.0) finish(P, S, HELM_OK, 0.0);
     }
   }
@@ -217,20 +268,23 @@ __device__ void phaseA_fp64(const KParams& P, int t, double* sh) {
   const KSys Y = P.sys[T.sys];
   const int amode = vload(&S->amode);
   const cd* src = amode ? Y.r : Y.p;
-  const int gid = threadIdx.x / G64, g = threadIdx.x % G64;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
-    const int64_t row = base + gid;
-    const bool valid = row < T.row1;
-    const cd s = csr_row27<G64, double>(Y.rowptr, Y.col, Y.val, src, row, valid, g);
-    if (valid && g == 0) {
-      Y.q[row] = s;
-      const cd pi = src[row];
-      if (amode) Y.p[row] = pi;
-      v[0] += pi.re * s.re - pi.im * s.im;
-      v[1] += pi.re * s.im + pi.im * s.re;
-    }
-  }
+  tile_spmv<double>(
+      Y.val, Y.cflag, src, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
+      [&](int64_t row, cd q, int) {
+        Y.q[row] = q;
+        const cd pi = src[row];
+        if (amode) Y.p[row] = pi;
+        v[0] += pi.re * q.re - pi.im * q.im;
+        v[1] += pi.re * q.im + pi.im * q.re;
+      },
+      [&](int64_t row, cd qi) {
+        const cd q0 = Y.q[row];
+        Y.q[row] = cd(q0.re + qi.re, q0.im + qi.im);
+        const cd pi = src[row];
+        v[0] += pi.re * qi.re - pi.im * qi.im;
+        v[1] += pi.re * qi.im + pi.im * qi.re;
+      });
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
   if (arrive_last(S, Y.ntiles)) {
@@ -257,7 +311,7 @@ __device__ void phaseB_fp64(const KParams& P, int t, double* sh) {
   const cd al = S->alpha;
   const cd mal(-al.re, -al.im);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  constexpr int U = 4;  // rows per thread per pass: all loads issued before the arithmetic
+  constexpr int U = HELM_VEC_UNROLL;  // rows per thread per pass: all loads issued before the arithmetic
   for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
     cd pv[U], qv[U], xv[U], rv[U];
 #pragma unroll
@@ -312,7 +366,7 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
   const KSys Y = P.sys[T.sys];
   if (vload(&S->cmode) == C_PUPDATE) {
     const cd be = S->beta;
-    constexpr int U = 4;
+    constexpr int U = HELM_VEC_UNROLL;
     for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
       cd rv[U], pv[U];
 #pragma unroll
@@ -335,21 +389,26 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
     return;
   }
   // true residual r = b - A x
-  const int gid = threadIdx.x / G64, g = threadIdx.x % G64;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
-    const int64_t row = base + gid;
-    const bool valid = row < T.row1;
-    const cd s = csr_row27<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
-    if (valid && g == 0) {
-      const cd bi = Y.b[row];
-      const cd ri(bi.re - s.re, bi.im - s.im);
-      Y.r[row] = ri;
-      v[0] += ri.re * ri.re - ri.im * ri.im;
-      v[1] += 2.0 * ri.re * ri.im;
-      v[2] += ri.re * ri.re + ri.im * ri.im;
-    }
-  }
+  auto add = [&](cd ri) {
+    v[0] += ri.re * ri.re - ri.im * ri.im;
+    v[1] += 2.0 * ri.re * ri.im;
+    v[2] += ri.re * ri.re + ri.im * ri.im;
+  };
+  tile_spmv<double>(
+      Y.val, Y.cflag, Y.x, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
+      [&](int64_t row, cd s, int c) {
+        const cd bi = Y.b[row];
+        const cd ri(bi.re - s.re, bi.im - s.im);
+        Y.r[row] = ri;
+        if (!c) add(ri);
+      },
+      [&](int64_t row, cd si) {
+        const cd r0 = Y.r[row];
+        const cd ri(r0.re - si.re, r0.im - si.im);
+        Y.r[row] = ri;
+        add(ri);
+      });
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
   if (arrive_last(S, Y.ntiles)) {
@@ -380,32 +439,49 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
   const KSys Y = P.sys[T.sys];
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (vload(&S->mode) == MODE_RESID) {
-    // FP64 true residual of the refinement
-    const int gid = threadIdx.x / G64, g = threadIdx.x % G64;
-    for (int64_t base = T.row0; base < T.row1; base += kBlock / G64) {
-      const int64_t row = base + gid;
-      const bool valid = row < T.row1;
-      const cd s = csr_row27<G64, double>(Y.rowptr, Y.col, Y.val, Y.x, row, valid, g);
-      if (valid && g == 0) {
-        const cd bi = Y.b[row];
-        const cd ri(bi.re - s.re, bi.im - s.im);
-        Y.r[row] = ri;
-        v[2] += ri.re * ri.re + ri.im * ri.im;
-      }
-    }
+    // FP64 true residual of the refinement (norm, and r^T r for a switch to FP64 COCG)
+    auto add = [&](cd ri) {
+      v[0] += ri.re * ri.re - ri.im * ri.im;
+      v[1] += 2.0 * ri.re * ri.im;
+      v[2] += ri.re * ri.re + ri.im * ri.im;
+    };
+    tile_spmv<double>(
+        Y.val, Y.cflag, Y.x, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
+        [&](int64_t row, cd s, int c) {
+          const cd bi = Y.b[row];
+          const cd ri(bi.re - s.re, bi.im - s.im);
+          Y.r[row] = ri;
+          if (!c) add(ri);
+        },
+        [&](int64_t row, cd si) {
+          const cd r0 = Y.r[row];
+          const cd ri(r0.re - si.re, r0.im - si.im);
+          Y.r[row] = ri;
+          add(ri);
+        });
     block_sum<4>(v, sh);
     write_parts(P.part, t, v);
     if (arrive_last(S, Y.ntiles)) {
-      cd u, rr;
-      sum_parts(P.part, Y.tile0, Y.ntiles, u, rr, sh);
+      cd rho, rr;
+      sum_parts(P.part, Y.tile0, Y.ntiles, rho, rr, sh);
       if (threadIdx.x == 0) {
         const double rel = sqrt(rr.re) / S->bnorm;
         S->relres = rel;
         S->pend = 0;
+        S->to_fp64 = 0;
         if (rel <= P.tol) { S->pend = 1; S->status = HELM_OK; }
         else if (!(rel == rel)) { S->pend = 1; S->status = HELM_NAN; }
         else if (S->outer >= P.max_outer || S->it >= P.maxit) { S->pend = 1; S->status = HELM_NOT_CONVERGED; }
-        else { S->rnorm = sqrt(rr.re); S->outer += 1; }
+        else if (S->outer >= 1 && rel > 0.5 * S->prev_rel) {
+          // complex64 refinement stalls on this system: continue with FP64 COCG from x, or
+          // from x = 0 if the refinement left x worse than zero (phase B then sets r = b)
+          S->to_fp64 = 1;
+          S->reset_x = rel > 1.0;
+          S->rho = rho;
+          S->amode = 1;
+          S->bd = 0;
+        } else { S->rnorm = sqrt(rr.re); S->outer += 1; }
+        S->prev_rel = rel;
       }
     }
     return;
@@ -413,19 +489,25 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
   // inner complex64 step: q32 = A32 src
   const int amode = vload(&S->amode);
   const cf* src = amode ? Y.r32 : Y.p32;
-  const int gid = threadIdx.x / G32, g = threadIdx.x % G32;
-  for (int64_t base = T.row0; base < T.row1; base += kBlock / G32) {
-    const int64_t row = base + gid;
-    const bool valid = row < T.row1;
-    const cf s = csr_row27<G32, float>(Y.rowptr, Y.col, Y.val32, src, row, valid, g);
-    if (valid && g == 0) {
-      Y.q32[row] = s;
-      const cf pi = src[row];
-      if (amode) Y.p32[row] = pi;
-      v[0] += (double)(pi.re * s.re - pi.im * s.im);
-      v[1] += (double)(pi.re * s.im + pi.im * s.re);
-    }
-  }
+  float a0 = 0.f, a1 = 0.f;  // per-thread FP32 partial over its rows, FP64 from the block sum on
+  tile_spmv<float>(
+      Y.val32, Y.cflag, src, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
+      [&](int64_t row, cf q, int) {
+        Y.q32[row] = q;
+        const cf pi = src[row];
+        if (amode) Y.p32[row] = pi;
+        a0 += pi.re * q.re - pi.im * q.im;
+        a1 += pi.re * q.im + pi.im * q.re;
+      },
+      [&](int64_t row, cf qi) {
+        const cf q0 = Y.q32[row];
+        Y.q32[row] = cf(q0.re + qi.re, q0.im + qi.im);
+        const cf pi = src[row];
+        a0 += pi.re * qi.re - pi.im * qi.im;
+        a1 += pi.re * qi.im + pi.im * qi.re;
+      });
+  v[0] = a0;
+  v[1] = a1;
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
   if (arrive_last(S, Y.ntiles)) {
@@ -433,6 +515,7 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
     sum_parts(P.part, Y.tile0, Y.ntiles, mu, unused, sh);
     if (threadIdx.x == 0) {
       S->it += 1;
+      S->it32 += 1;
       S->inner_it += 1;
       const cd rho = S->rho;
       if ((mu.re == 0.0 && mu.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0)) {
@@ -453,6 +536,25 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (vload(&S->mode) == MODE_RESID) {
     if (vload(&S->pend)) return;
+    if (vload(&S->to_fp64)) {
+      if (!vload(&S->reset_x)) return;
+      // restart from x = 0: r = b, rho = b^T b
+      for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+        const cd bi = Y.b[i];
+        Y.x[i] = cd(0.0, 0.0);
+        Y.r[i] = bi;
+        v[0] += bi.re * bi.re - bi.im * bi.im;
+        v[1] += 2.0 * bi.re * bi.im;
+      }
+      block_sum<4>(v, sh);
+      write_parts(P.part, t, v);
+      if (arrive_last(S, Y.ntiles)) {
+        cd rho, unused;
+        sum_parts(P.part, Y.tile0, Y.ntiles, rho, unused, sh);
+        if (threadIdx.x == 0) S->rho = rho;
+      }
+      return;
+    }
     // start an inner solve on r / ||r|| (complex64), x32 = 0
     const double sc = 1.0 / S->rnorm;
     float a0 = 0.f, a1 = 0.f;
@@ -484,7 +586,7 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
   const cf a32((float)al.re, (float)al.im);
   const cf ma32(-a32.re, -a32.im);
   float acc[3] = {0.f, 0.f, 0.f};
-  constexpr int U = 4;
+  constexpr int U = HELM_VEC_UNROLL;
   for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
     cf pv[U], qv[U], xv[U], rv[U];
 #pragma unroll
@@ -526,6 +628,7 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
       S->amode = 0;
       if (!(est > P.inner_tol) || S->inner_it >= P.inner_maxit || S->it >= P.maxit || S->bd) {
         S->cmode = C_XUPDATE;
+        S->discard = !(est < 1.0);  // no reduction (or NaN): keep x, the residual test switches
       } else {
         S->beta = cdiv(rho_new, S->rho);
         S->rho = rho_new;
@@ -541,9 +644,10 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
   if (!vload(&S->act)) return;
   const KSys Y = P.sys[T.sys];
   if (vload(&S->mode) == MODE_RESID) {
-    const int pend = vload(&S->pend);
+    const int pend = vload(&S->pend), to64 = vload(&S->to_fp64);
     if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) {
       if (pend) finish(P, S, S->status, S->relres);
+      else if (to64) { S->mode = MODE_FP64; S->fell_back = 1; }
       else S->mode = MODE_INNER;
     }
     return;
@@ -551,7 +655,7 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
   if (vload(&S->cmode) == C_PUPDATE) {
     const cd be = S->beta;
     const cf b32((float)be.re, (float)be.im);
-    constexpr int U = 4;
+    constexpr int U = HELM_VEC_UNROLL;
     for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
       cf rv[U], pv[U];
 #pragma unroll
@@ -574,7 +678,7 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
     return;
   }
   // refinement update x += ||r|| * d (FP64)
-  const double sc = S->rnorm;
+  const double sc = vload(&S->discard) ? 0.0 : S->rnorm;
   for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
     const cf d = Y.x32[i];
     cd xi = Y.x[i];
@@ -583,6 +687,12 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
     Y.x[i] = xi;
   }
   if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) S->mode = MODE_RESID;
+}
+
+// A mixed-precision system that fell back to FP64 COCG (its mode changes only in phase C, after
+// every tile of the system has arrived, so all blocks see one mode per step).
+__device__ __forceinline__ bool in_fp64(const KParams& P, int t) {
+  return vload(&P.st[P.tiles[t].sys].mode) == MODE_FP64;
 }
 
 template <bool MIXED, int MINB>
@@ -601,18 +711,18 @@ __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
     bool rebuilt = false;
     if (blockIdx.x == 0) rebuilt = rebuild_list(P, cur, seen_fin, sh_int);
     for (int a = blockIdx.x; a < nat; a += nb) {
-      if (MIXED) phaseA_mixed(P, list[a], sh);
+      if (MIXED && !in_fp64(P, list[a])) phaseA_mixed(P, list[a], sh);
       else phaseA_fp64(P, list[a], sh);
     }
     if (!grid_barrier(P.bar, nb)) return;
     if (rebuilt && threadIdx.x == 0) P.ctrl[CTRL_CUR] = cur ^ 1;
     for (int a = blockIdx.x; a < nat; a += nb) {
-      if (MIXED) phaseB_mixed(P, list[a], sh);
+      if (MIXED && !in_fp64(P, list[a])) phaseB_mixed(P, list[a], sh);
       else phaseB_fp64(P, list[a], sh);
     }
     if (!grid_barrier(P.bar, nb)) return;
     for (int a = blockIdx.x; a < nat; a += nb) {
-      if (MIXED) phaseC_mixed(P, list[a], sh);
+      if (MIXED && !in_fp64(P, list[a])) phaseC_mixed(P, list[a], sh);
       else phaseC_fp64(P, list[a], sh);
     }
     if (!grid_barrier(P.bar, nb)) return;
@@ -656,12 +766,14 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   per_sm = std::min(per_sm, want);
   const int nblocks = nsm * per_sm;
 
-  // tiles: about nblocks tiles for a system that fills the GPU, 256-row multiples
+  // tiles: about nblocks tiles for a system that fills the GPU, multiples of 2 * kBlock rows
+  // (the SpMV phases give every thread a pair of rows)
   std::vector<KTile> tiles;
   std::vector<int> tile0(nsys), ntl(nsys);
+  const int64_t TQ = 2 * kBlock;
   for (int k = 0; k < nsys; ++k) {
     const int64_t n = sys[k].ctx->n;
-    const int64_t per = 256 * std::max<int64_t>(1, (n + 256LL * nblocks - 1) / (256LL * nblocks));
+    const int64_t per = TQ * std::max<int64_t>(1, (n + TQ * nblocks - 1) / (TQ * nblocks));
     tile0[k] = (int)tiles.size();
     for (int64_t r0 = 0; r0 < n; r0 += per) tiles.push_back(KTile{k, 0, r0, std::min(n, r0 + per)});
     ntl[k] = (int)tiles.size() - tile0[k];
@@ -671,10 +783,10 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   // one arena for every per-system buffer plus the control data
   size_t bytes = 0;
   for (int k = 0; k < nsys; ++k) {
-    const size_t n = sys[k].ctx->n, nnz = sys[k].ctx->nnz;
-    bytes += rnd(nnz * sizeof(cd)) + rnd(n * sizeof(cd)) * 2;  // val, b, r
+    const size_t n = sys[k].ctx->n, nnz = 27 * n;  // slot-major 27-point values
+    bytes += rnd(nnz * sizeof(cd)) + rnd(n * sizeof(cd)) * 2 + rnd(n);  // val, b, r, row flags
     if (mixed) bytes += rnd(nnz * sizeof(cf)) + 4 * rnd(n * sizeof(cf));
-    else bytes += 2 * rnd(n * sizeof(cd));  // p, q
+    bytes += 2 * rnd(n * sizeof(cd));  // p, q (FP64 COCG, also the fallback of the mixed solver)
   }
   bytes += rnd(nsys * sizeof(KSys)) + rnd(nsys * sizeof(KState)) + rnd(ntiles * sizeof(KTile)) +
            2 * rnd(ntiles * sizeof(int)) + rnd(CTRL_N * sizeof(int)) + rnd(2 * (size_t)ntiles * sizeof(cd)) +
@@ -694,33 +806,34 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     KSys& Y = hs[k];
     memset(&Y, 0, sizeof(Y));
     Y.n = c->n;
-    Y.rowptr = c->rowptr;
-    Y.col = c->col;
-    cd* val = A.take<cd>(c->nnz);
+    Y.Nx = c->mesh.nx + 1;
+    Y.NxNy = Y.Nx * (c->mesh.ny + 1);
+    cd* val = A.take<cd>(27 * (size_t)c->n);
     cd* b = A.take<cd>(c->n);
+    uint8_t* cflag = A.take<uint8_t>(c->n);
+    Y.cflag = cflag;
     Y.val = val;
     Y.b = b;
     Y.x = sys[k].p_out;
     Y.r = A.take<cd>(c->n);
     if (mixed) {
-      cf* v32 = A.take<cf>(c->nnz);
+      cf* v32 = A.take<cf>(27 * (size_t)c->n);
       Y.val32 = v32;
       Y.x32 = A.take<cf>(c->n);
       Y.r32 = A.take<cf>(c->n);
       Y.p32 = A.take<cf>(c->n);
       Y.q32 = A.take<cf>(c->n);
-    } else {
-      Y.p = A.take<cd>(c->n);
-      Y.q = A.take<cd>(c->n);
     }
+    Y.p = A.take<cd>(c->n);
+    Y.q = A.take<cd>(c->n);
     Y.tile0 = tile0[k];
     Y.ntiles = ntl[k];
-    st = assemble_values(c, sys[k].freq, val, b, s);
+    st = assemble_values(c, sys[k].freq, val, b, s, true, /*dia=*/true, cflag);
     if (st == HELM_OK && sys[k].rhs) {
       cudaError_t ce = cudaMemcpyAsync(b, sys[k].rhs, c->n * sizeof(cd), cudaMemcpyDeviceToDevice, s);
       if (ce != cudaSuccess) st = cuda_error(ce, "rhs copy");
     }
-    if (st == HELM_OK && mixed) st = cast_values(val, const_cast<cf*>(Y.val32), c->nnz, s);
+    if (st == HELM_OK && mixed) st = cast_values(val, const_cast<cf*>(Y.val32), 27 * c->n, s);
     if (st != HELM_OK) {
       cudaFree(A.base);
       return st;
@@ -804,7 +917,9 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     if (hb.status & DEV_TIMEOUT) S.status = HELM_TIMEOUT;
     S.iterations = K.it;
     S.restarts = K.restarts;
-    S.outer = K.outer;
+    S.outer = K.fell_back ? -K.outer : K.outer;
+    S.iterations_c64 = K.it32;
+    S.pad = 0;
     S.relres = K.relres;
     S.bnorm = K.bnorm;
     if (S.status != HELM_OK && overall == HELM_OK) overall = (helm_status)S.status;

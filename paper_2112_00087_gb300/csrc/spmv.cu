@@ -37,6 +37,34 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(const int32_t* __restrict_
   }
 }
 
+// y = A x in the slot-major 27-point layout, one thread per row (block-uniform grid-stride):
+// real parts for every row, then, if any row of the block is flagged complex, its imaginary
+// parts in a second pass.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) spmv_dia_kernel(const cplx<T>* __restrict__ val,
+                                                          const uint8_t* __restrict__ cflag,
+                                                          const cplx<T>* __restrict__ x,
+                                                          cplx<T>* __restrict__ y, int64_t n, int64_t Nx,
+                                                          int64_t NxNy) {
+  for (int64_t base = blockIdx.x * (int64_t)kBlock; base < n; base += (int64_t)gridDim.x * kBlock) {
+    const int64_t row = base + threadIdx.x;
+    const bool valid = row < n;
+    cplx<T> s(T(0), T(0));
+    int c = 0;
+    if (valid) {
+      s = dia_row_re<T>(val, x, n, Nx, NxNy, row);
+      c = cflag[row];
+    }
+    if (__syncthreads_or(c)) {
+      if (c) {
+        const cplx<T> si = dia_row_im<T>(val, x, n, Nx, NxNy, row);
+        s = cplx<T>(s.re + si.re, s.im + si.im);
+      }
+    }
+    if (valid) y[row] = s;
+  }
+}
+
 // Stage 1: block b sums the contiguous chunk [b*chunk, (b+1)*chunk) (threads strided inside).
 __global__ void __launch_bounds__(kBlock) reduce_stage1(int op, const cd* __restrict__ x,
                                                          const cd* __restrict__ y, int64_t n,
@@ -95,6 +123,24 @@ helm_status spmv_c64(const int32_t* rowptr, const int32_t* col, const cf* val, c
   constexpr int G = 8;
   int64_t blocks = std::min<int64_t>((n + kBlock / G - 1) / (kBlock / G), (int64_t)num_sms() * 8);
   spmv_kernel<G, float><<<(unsigned)blocks, kBlock, 0, s>>>(rowptr, col, val, x, y, n);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+helm_status spmv_dia_c128(const cd* val, const uint8_t* cflag, const cd* x, cd* y, int64_t n, int64_t Nx,
+                          int64_t NxNy, cudaStream_t s) {
+  if (n == 0) return HELM_OK;
+  int64_t blocks = std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)num_sms() * 8);
+  spmv_dia_kernel<double><<<(unsigned)blocks, kBlock, 0, s>>>(val, cflag, x, y, n, Nx, NxNy);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+helm_status spmv_dia_c64(const cf* val, const uint8_t* cflag, const cf* x, cf* y, int64_t n, int64_t Nx,
+                         int64_t NxNy, cudaStream_t s) {
+  if (n == 0) return HELM_OK;
+  int64_t blocks = std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)num_sms() * 8);
+  spmv_dia_kernel<float><<<(unsigned)blocks, kBlock, 0, s>>>(val, cflag, x, y, n, Nx, NxNy);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }

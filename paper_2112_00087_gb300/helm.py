@@ -21,12 +21,13 @@ HELM_BREAKDOWN, HELM_NAN, HELM_PIVOT, HELM_TIMEOUT, HELM_ERR_STATE = 5, 6, 7, 8,
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
                 6: "NAN", 7: "PIVOT", 8: "TIMEOUT", 9: "ERR_STATE"}
 HELM_C128, HELM_C64 = 0, 1
+HELM_FMT_CSR, HELM_FMT_DIA27 = 0, 1
 HELM_SOLVER_GMRES, HELM_SOLVER_COCG = 0, 1
 HELM_PRECOND_NONE, HELM_PRECOND_RAS = 0, 1
 
 # Symbols declared in include/helm.h (tests check the library exports all of them).
 EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary", "helm_sizes",
-            "helm_assemble", "helm_matrix_free", "helm_matrix_csr", "helm_spmv", "helm_reduce",
+            "helm_assemble", "helm_matrix_free", "helm_matrix_csr", "helm_matrix_dia27", "helm_spmv", "helm_reduce",
             "helm_solve", "helm_solve_batch", "helm_adjoint_grad", "helm_adjoint_seed", "helm_last_profile",
             "helm_reduce_noalloc"]
 
@@ -63,10 +64,11 @@ class Profile(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
-                ("outer", ctypes.c_int32), ("relres", ctypes.c_double), ("bnorm", ctypes.c_double)]
+                ("outer", ctypes.c_int32), ("relres", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("iterations_c64", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 def _load():
@@ -82,9 +84,10 @@ def _load():
         "helm_destroy": (None, [vp]),
         "helm_set_boundary": (i32, [vp, vp, vp, i32, vp]),
         "helm_sizes": (i32, [vp, P(i64), P(i64), P(i64), P(i32)]),
-        "helm_assemble": (i32, [vp, d, i32, P(vp), vp]),
+        "helm_assemble": (i32, [vp, d, i32, i32, P(vp), vp]),
         "helm_matrix_free": (None, [vp]),
         "helm_matrix_csr": (i32, [vp, P(i64), P(i64), P(i32), P(vp), P(vp), P(vp)]),
+        "helm_matrix_dia27": (i32, [vp, P(i64), P(i32), P(vp)]),
         "helm_spmv": (i32, [vp, vp, vp, vp]),
         "helm_reduce": (i32, [i32, i64, vp, vp, P(d), vp]),
         "helm_reduce_noalloc": (i32, [i32, i64, vp, vp, P(d), vp]),
@@ -186,15 +189,16 @@ class Context:
 
 
 class Matrix:
-    """helm_assemble result; .csr() copies rowptr / col / values into torch tensors."""
+    """helm_assemble result; .csr() / .dia27() copy the stored values into torch tensors."""
 
-    def __init__(self, ctx: Context, freq: float, precision=HELM_C128, with_rhs=True):
+    def __init__(self, ctx: Context, freq: float, precision=HELM_C128, with_rhs=True, fmt=HELM_FMT_CSR):
         self.ctx = ctx
         h = ctypes.c_void_p()
         self.rhs = torch.empty(ctx.n, dtype=torch.complex128, device="cuda") if with_rhs else None
-        _check(LIB.helm_assemble(ctx.handle, float(freq), precision, ctypes.byref(h), _ptr(self.rhs)))
+        _check(LIB.helm_assemble(ctx.handle, float(freq), precision, fmt, ctypes.byref(h), _ptr(self.rhs)))
         self.handle = h
         self.precision = precision
+        self.format = fmt
         self.n, self.nnz = ctx.n, ctx.nnz
 
     def csr(self):
@@ -211,6 +215,16 @@ class Matrix:
         _cuda_copy(col, cl.value)
         _cuda_copy(val, vl.value)
         return rowptr, col, val
+
+    def dia27(self):
+        """Values [27, n] (slot k = (di+1) + 3(dj+1) + 9(dl+1))."""
+        n, prec, vl = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_void_p()
+        _check(LIB.helm_matrix_dia27(self.handle, ctypes.byref(n), ctypes.byref(prec), ctypes.byref(vl)))
+        vdt = torch.complex64 if prec.value == HELM_C64 else torch.complex128
+        val = torch.empty(27 * n.value, dtype=vdt, device="cuda")
+        torch.cuda.synchronize()
+        _cuda_copy(val, vl.value)
+        return val.reshape(27, n.value)
 
     def free(self):
         if self.handle is not None and self.handle.value:
@@ -256,8 +270,8 @@ def helm_set_boundary(ctx: Context, beta, dir_nodes, p_dir):
     ctx.set_boundary(beta, dir_nodes, p_dir)
 
 
-def helm_assemble(ctx: Context, freq: float, precision=HELM_C128, with_rhs=True) -> Matrix:
-    return Matrix(ctx, freq, precision, with_rhs)
+def helm_assemble(ctx: Context, freq: float, precision=HELM_C128, with_rhs=True, fmt=HELM_FMT_CSR) -> Matrix:
+    return Matrix(ctx, freq, precision, with_rhs, fmt)
 
 
 def helm_spmv(A: Matrix, x: torch.Tensor, y: torch.Tensor, stream=None):

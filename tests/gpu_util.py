@@ -26,3 +26,18 @@ def gpu_matrix(ctx, freq, precision=helm.HELM_C128):
 
 def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def dia_to_scipy(val27, mesh):
+    """Slot-major [27, n] values -> scipy CSR (zero slots dropped), slot k = (di+1)+3(dj+1)+9(dl+1)."""
+    v = val27.cpu().numpy()
+    n = v.shape[1]
+    Nx, Ny = mesh.nx + 1, mesh.ny + 1
+    rows, cols, vals = [], [], []
+    r = np.arange(n)
+    for k in range(27):
+        di, dj, dl = k % 3 - 1, (k // 3) % 3 - 1, k // 9 - 1
+        c = r + di + Nx * (dj + Ny * dl)
+        m = v[k] != 0
+        rows.append(r[m]); cols.append(c[m]); vals.append(v[k][m])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))

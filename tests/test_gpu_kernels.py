@@ -15,7 +15,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_2112_00087_gb300 import helm  # noqa: E402
-from tests.gpu_util import context, gpu_matrix, rel  # noqa: E402
+from tests.gpu_util import context, dia_to_scipy, gpu_matrix, rel  # noqa: E402
 
 
 CASES = [
@@ -70,6 +70,43 @@ def test_spmv_c128_and_c64(name, prob, f):
     u = 2.0 ** -24
     err32 = np.abs(y32.cpu().numpy().astype(np.complex128) - yref)
     assert np.all(err32 <= 64 * u * absbound + 1e-30)
+
+
+@pytest.mark.parametrize("name,prob,f", CASES, ids=[c[0] for c in CASES])
+def test_dia27_layout_assembly_and_spmv(name, prob, f):
+    """Slot-major 27-point layout: same matrix as the oracle, padded slots zero, SpMV parity."""
+    ctx = context(prob)
+    A = helm.helm_assemble(ctx, f, fmt=helm.HELM_FMT_DIA27)
+    v27 = A.dia27()
+    m = prob.mesh
+    # slots whose neighbour lies outside the lattice hold zero
+    vv = v27.cpu().numpy()
+    n = ctx.n
+    r = np.arange(n)
+    i, j, l = r % (m.nx + 1), (r // (m.nx + 1)) % (m.ny + 1), r // ((m.nx + 1) * (m.ny + 1))
+    for k in range(27):
+        di, dj, dl = k % 3 - 1, (k // 3) % 3 - 1, k // 9 - 1
+        outside = (i + di < 0) | (i + di > m.nx) | (j + dj < 0) | (j + dj > m.ny) | (l + dl < 0) | (l + dl > m.nz)
+        assert np.all(vv[k][outside] == 0)
+    S = dia_to_scipy(v27, m)
+    Aref, bref = fem.system(prob, f)
+    assert abs(S - Aref).max() <= 1e-14 * abs(Aref).max()
+    assert np.max(np.abs(A.rhs.cpu().numpy() - bref)) <= 1e-14 * np.max(np.abs(bref))
+    x = hi.random_complex(n, seed=9)
+    xg = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xg)
+    helm.helm_spmv(A, xg, y)
+    torch.cuda.synchronize()
+    yref = Aref @ x
+    absbound = abs(Aref) @ np.abs(x)
+    assert np.all(np.abs(y.cpu().numpy() - yref) <= 1e-13 * absbound + 1e-300)
+    A32 = helm.helm_assemble(ctx, f, helm.HELM_C64, with_rhs=False, fmt=helm.HELM_FMT_DIA27)
+    x32 = xg.to(torch.complex64)
+    y32 = torch.empty_like(x32)
+    helm.helm_spmv(A32, x32, y32)
+    torch.cuda.synchronize()
+    err32 = np.abs(y32.cpu().numpy().astype(np.complex128) - yref)
+    assert np.all(err32 <= 64 * 2.0 ** -24 * absbound + 1e-30)
 
 
 @pytest.mark.parametrize("n", [1, 255, 1000, 1 << 20, (1 << 20) + 77])
