@@ -3,15 +3,17 @@
 Workload (default "sweep256"): 256 log-spaced frequencies 20-500 Hz, each solved on its own
 wavelength-scaled 2.5 x 1.4 x 1.2 m cabin lattice (24x14x12 .. 148x83x71 bricks, 25.17 M nodes
 in total) with the sun-roof Dirichlet pressure and random seat admittances, to a true FP64
-relative residual of 1e-10. One step = assembly + lifting + solve of all 256 systems in one
-call (helm_solve_batch: one persistent cooperative launch), batched + mixed precision
-(complex64 inner COCG, FP64 refinement). Inputs (lattices, boundary data) are resident on the
-device before timing; the 13 GB of matrices the step assembles exceed L2, so no flush is needed.
+relative residual of 1e-10. One step = assembly + lifting + COCG solve of all 256 systems in
+one call (helm_solve_batch: one persistent cooperative launch). Inputs (lattices, boundary
+data) are resident on the device before timing; the 10.9 GB of matrix values the step
+assembles exceed L2, so no flush is needed.
 
-Extra measurements in the same line: the plain FP64 solver on the same sweep (batched and
-one-frequency-at-a-time), the SpMV roofline on the 2,203,161-node lattice (complex128 and
-complex64, L2 flushed), the end-to-end figure through host buffers, and the CPU oracle on a
-bounded sample (cpu_baseline). `--impl reference` times the CPU oracle alone.
+The main (timed) leg is the batched FP64 solver; the same line reports the batched
+mixed-precision solver (complex64 inner COCG, FP64 refinement, per-system FP64 fallback), the
+plain FP64 solver run one frequency per call, the SpMV roofline on the 2,203,161-node lattice
+(CSR and slot-major layouts, complex128 and complex64, L2 flushed), the end-to-end figure
+through host buffers, and the CPU oracle on a bounded sample (cpu_baseline). `--mixed` makes
+the mixed solver the timed leg; `--impl reference` times the CPU oracle alone.
 """
 from __future__ import annotations
 
@@ -260,10 +262,14 @@ def run_gpu(args):
 
     freqs, probs, ctxs, outs = build_sweep(args.nfreq, helm, torch, args.workload)
     nsys = len(ctxs)
-    mo = mixed_opts(helm, args.maxit) if not args.fp64 else fp64_opts(helm, args.maxit)
+    main_mixed = args.mixed
+    mo = mixed_opts(helm, args.maxit)
+    fo = fp64_opts(helm, args.maxit)
+    main_opts = mo if main_mixed else fo
+    bytes_fn = cocg_mixed_bytes if main_mixed else cocg_fp64_bytes
 
     def step():
-        _, st = helm.helm_solve_batch(ctxs, freqs, mo, outs, raise_on_fail=False)
+        _, st = helm.helm_solve_batch(ctxs, freqs, main_opts, outs, raise_on_fail=False)
         return st, helm.helm_last_profile()
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
@@ -284,62 +290,56 @@ def run_gpu(args):
     value = world * nsys * args.steps / secs
 
     # roofline of the dominant kernel (the persistent solve), from the last timed step
-    alg = sum((cocg_fp64_bytes if args.fp64 else cocg_mixed_bytes)(c.n, c.nnz, s) for c, s in zip(ctxs, stats))
+    alg = sum(bytes_fn(c.n, c.nnz, s) for c, s in zip(ctxs, stats))
     kern_s = prof["solve_ms"] / 1e3
     achieved = alg / kern_s / 1e9
     launches = sum(p["launches"] for _, p in results)
-
+    desc = ("sweep256: %d log-spaced frequencies 20-500 Hz, each on its own wavelength-scaled 2.5x1.4x1.2 m "
+            "cabin lattice (24x14x12..148x83x71, %d nodes total), sun-roof Dirichlet pressure + random seat "
+            "admittance; assembly + lifting + COCG to true rel-res 1e-10 for all systems in one persistent "
+            "launch" % (nsys, sum(c.n for c in ctxs))) if args.workload == "sweep256" else args.workload
     out = {"metric": METRIC, "value": value, "unit": "freqs/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64-inner/c128-outer", "data": "synthetic",
-           "config": {"workload": "sweep256: %d log-spaced frequencies 20-500 Hz, each on its own wavelength-scaled "
-                                  "2.5x1.4x1.2 m cabin lattice (24x14x12..148x83x71, %d nodes total), sun-roof "
-                                  "Dirichlet pressure + random seat admittance; COCG, complex64 inner / FP64 "
-                                  "refinement, true rel-res 1e-10; batched in one persistent launch" %
-                                  (nsys, sum(c.n for c in ctxs)),
-                      "l2": "inputs larger than L2 (%.1f GB of CSR assembled per step)" %
-                            (sum(c.nnz * 32 for c in ctxs) / 1e9),
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64-inner/c128-outer" if main_mixed else "c128",
+           "data": "synthetic",
+           "config": {"workload": desc, "precision": "mixed (complex64 inner, FP64 refinement)" if main_mixed
+                      else "fp64 (batched; the mixed mode is reported under 'mixed')",
+                      "l2": "inputs larger than L2 (%.1f GB of matrix values assembled per step)" %
+                            (sum(c.n * 27 * 16 for c in ctxs) / 1e9),
                       "parallelism": "replicas" if world > 1 else "1 GPU"},
            "converged": "%d/%d" % (n_ok, nsys),
            "iterations": {"total": int(sum(s["iterations"] for s in stats)),
                           "c64_total": int(sum(s["iterations_c64"] for s in stats)),
                           "max": int(max(s["iterations"] for s in stats)),
-                          "fell_back_to_fp64": int(sum(1 for s in stats if s["outer"] < 0)),
                           "relres_max": max(s["relres"] for s in stats)},
            "phases_ms": {"assemble": prof["assemble_ms"], "solve": prof["solve_ms"]},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                         "frac": achieved / peak_gbs, "traffic": None,
-                        "kernel": "cocg_persistent<mixed>", "algorithmic_bytes": alg,
-                        "kernel_ms": prof["solve_ms"], "peak_kind": peak_kind},
+                        "kernel": "cocg_persistent<%s>" % ("mixed" if main_mixed else "fp64"),
+                        "algorithmic_bytes": alg, "kernel_ms": prof["solve_ms"], "peak_kind": peak_kind},
            "gpu_launches": int(launches), "clocks": clk}
 
-    if args.verbose and rank == 0:
-        for c, f, st_ in zip(ctxs, freqs, stats):
-            print("sys f=%7.2f n=%8d its=%6d c64=%6d outer=%3d restarts=%3d status=%d relres=%.2e" %
-                  (f, c.n, st_["iterations"], st_["iterations_c64"], st_["outer"], st_["restarts"], st_["status"],
-                   st_["relres"]),
-                  file=sys.stderr, flush=True)
     if rank == 0 and not args.quick:
-        # plain FP64 on the same sweep: batched (one launch) and one frequency at a time
-        fo = fp64_opts(helm)
+        # the other precision, batched, timed once
+        other = fo if main_mixed else mo
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
+        _, st2 = helm.helm_solve_batch(ctxs, freqs, other, outs, raise_on_fail=False)
         torch.cuda.synchronize()
-        _, st64 = helm.helm_solve_batch(ctxs, freqs, fo, outs, raise_on_fail=False)
-        torch.cuda.synchronize()
-        t_b = time.perf_counter() - t0
-        prof64 = helm.helm_last_profile()
-        alg64 = sum(cocg_fp64_bytes(c.n, c.nnz, s) for c, s in zip(ctxs, st64))
-        res = {"batched_freqs_per_s": nsys / t_b, "converged": sum(1 for s in st64 if s["status"] == 0),
-               "iterations_total": int(sum(s["iterations"] for s in st64)),
-               "kernel_gbs": alg64 / (prof64["solve_ms"] / 1e3) / 1e9}
+        t2 = time.perf_counter() - t0
+        key = "plain_fp64_batched" if main_mixed else "mixed"
+        out[key] = {"freqs_per_s": nsys / t2, "converged": sum(1 for s in st2 if s["status"] == 0),
+                    "iterations_total": int(sum(s["iterations"] for s in st2)),
+                    "c64_iterations": int(sum(s["iterations_c64"] for s in st2)),
+                    "fell_back_to_fp64": int(sum(1 for s in st2 if s["outer"] < 0))}
         if not args.no_sequential:
+            # plain FP64, one frequency per call (no batching)
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
             for c, f, o in zip(ctxs, freqs, outs):
                 helm.helm_solve_batch([c], [f], fo, [o], raise_on_fail=False)
             torch.cuda.synchronize()
-            res["sequential_freqs_per_s"] = nsys / (time.perf_counter() - t0)
-        out["plain_fp64"] = res
-        out["speedup_mixed_vs_fp64_batched"] = value / res["batched_freqs_per_s"]
+            out["plain_fp64_sequential"] = {"freqs_per_s": nsys / (time.perf_counter() - t0)}
         out["spmv"] = spmv_roofline(helm, torch, peak_gbs)
 
         # end to end through host buffers: boundary data in from pinned memory, pressures out
@@ -352,21 +352,24 @@ def run_gpu(args):
         def e2e_step():
             for c, (b, d, q) in zip(ctxs, hb):
                 c.set_boundary(b.cuda(non_blocking=True), d.cuda(non_blocking=True), q.cuda(non_blocking=True))
-            helm.helm_solve_batch(ctxs, freqs, mo, outs, raise_on_fail=False)
+            helm.helm_solve_batch(ctxs, freqs, main_opts, outs, raise_on_fail=False)
             for o, h in zip(outs, hout):
                 h.copy_(o, non_blocking=True)
             torch.cuda.synchronize()
-        e2e_step()
         t0 = time.perf_counter()
-        for _ in range(max(1, args.steps)):
-            e2e_step()
-        e2e_s = (time.perf_counter() - t0) / max(1, args.steps)
+        e2e_step()
+        e2e_s = time.perf_counter() - t0
         out["e2e"] = {"value": nsys / e2e_s, "unit": "freqs/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
+    if args.verbose and rank == 0:
+        for c, f, st_ in zip(ctxs, freqs, stats):
+            print("sys f=%7.2f n=%8d its=%6d c64=%6d outer=%3d restarts=%3d status=%d relres=%.2e" %
+                  (f, c.n, st_["iterations"], st_["iterations_c64"], st_["outer"], st_["restarts"], st_["status"],
+                   st_["relres"]), file=sys.stderr, flush=True)
     if rank == 0 and not args.no_cpu:
-        done, t_cpu, cores, desc = cpu_oracle_sample(args.cpu_budget, args.nfreq)
+        done, t_cpu, cores, desc_cpu = cpu_oracle_sample(args.cpu_budget, args.nfreq)
         out["cpu_baseline"] = {"value": len(done) / t_cpu, "unit": "freqs/s", "cores": cores, "kind": "oracle",
-                               "sample": desc}
+                               "sample": desc_cpu}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -400,7 +403,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nfreq", type=int, default=256, help="frequencies of the sweep (256 = full workload)")
@@ -410,8 +413,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", default="sweep256", choices=["sweep256", "cabin2m", "cabin282k"],
                     help="sweep256 is the benchmark; the one-lattice cases serve profiling")
-    ap.add_argument("--maxit", type=int, default=400000, help="Krylov step cap (profiling captures)")
-    ap.add_argument("--fp64", action="store_true", help="time the plain FP64 solver as the main leg")
+    ap.add_argument("--maxit", type=int, default=30000, help="Krylov step cap per system")
+    ap.add_argument("--mixed", action="store_true", help="time the mixed-precision solver as the main leg")
+    ap.add_argument("--fp64", action="store_true", help="(default) time the FP64 solver as the main leg")
     ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
     args = ap.parse_args()
     if args.impl == "reference":

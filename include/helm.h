@@ -75,12 +75,16 @@ typedef struct {
   int32_t ras_parts[3]; /* Schwarz blocks along x, y, z */
   int32_t ras_overlap;  /* lattice layers of overlap */
   int32_t mixed;        /* 1: FP64 iterative refinement around a complex64 inner COCG (COCG only);
-                           a system whose refinement step fails to halve the FP64 residual
-                           continues as FP64 COCG from its current iterate (stats.outer < 0 marks
-                           such a fallback: -outer refinement steps were taken before it) */
+                           a system whose refinement step fails to halve the FP64 residual is
+                           restarted as FP64 COCG from zero (stats.outer < 0 marks such a
+                           fallback: -outer refinement steps were taken before it) */
   double inner_tol;     /* mixed: inner relative residual reduction per refinement step */
   int32_t inner_maxit;  /* mixed: inner steps per refinement step */
   int32_t max_outer;    /* mixed: refinement steps before HELM_NOT_CONVERGED */
+  int32_t stall_window; /* COCG: if the residual estimate has not halved its best value within
+                           this many steps, check the true residual and restart from the current
+                           iterate (0 = never; counted in stats.restarts) */
+  int32_t pad_;
 } helm_solve_opts;
 
 typedef struct {

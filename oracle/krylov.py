@@ -15,7 +15,8 @@ by step in complex128 numpy, the two iterations the GPU path runs:
 * ``cocg``: conjugate orthogonal CG (van der Vorst & Melissen 1990) for complex-symmetric
   A: CG with the unconjugated bilinear form x^T y. Stop when ||r_rec||/||b|| <= tol, then
   the true residual is checked; if it misses tol the iteration restarts from the current
-  x with r = b - A x.
+  x with r = b - A x. Optional stagnation rule (``stall``): when the estimate has not halved
+  its best value within ``stall`` steps, the same check-and-restart is taken.
 
 Iteration count = number of Krylov steps (products with A inside the iteration; the
 true-residual products are not counted).
@@ -147,7 +148,7 @@ def gmres(matvec, b, m, tol=1e-10, maxit=10000, precond=None, ortho="cgs2", x0=N
         st.restarts += 1
 
 
-def cocg(matvec, b, tol=1e-10, maxit=100000):
+def cocg(matvec, b, tol=1e-10, maxit=100000, stall=None):
     """COCG for complex-symmetric A. Returns (x, Stats)."""
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
@@ -158,6 +159,7 @@ def cocg(matvec, b, tol=1e-10, maxit=100000):
         st.converged, st.relres = True, 0.0
         return x, st
     r = b.copy()
+    best, best_it = 1.0, 0
     while True:
         p = r.copy()
         rho = dotu(r, r)
@@ -173,7 +175,9 @@ def cocg(matvec, b, tol=1e-10, maxit=100000):
             r = r - alpha * q
             est = nrm2(r) / nb
             st.history.append(est)
-            if est <= tol:
+            if est < 0.5 * best:
+                best, best_it = est, st.iterations
+            if est <= tol or (stall and st.iterations - best_it >= stall):
                 break
             rho_new = dotu(r, r)
             p = r + (rho_new / rho) * p
@@ -186,3 +190,4 @@ def cocg(matvec, b, tol=1e-10, maxit=100000):
         if st.iterations >= maxit or st.breakdown:
             return x, st
         st.restarts += 1
+        best, best_it = st.relres, st.iterations

@@ -6,15 +6,16 @@
 //   q = A p, alpha = rho / p^T q, x += alpha p, r -= alpha q, rho' = r^T r, beta = rho'/rho,
 //   p = r + beta p;
 // stop when ||r|| / ||b|| <= tol, confirm with the true residual b - A x, restart from x with
-// p = r if it misses tol.
+// p = r if it misses tol. Optional stagnation rule: if the estimate has not halved its best
+// value within `stall_window` steps, the same check-and-restart is taken.
 //
 // Mixed precision (FP64 iterative refinement, complex64 inner solve): r = b - A x in FP64,
 // inner COCG on A d = r / ||r|| with complex64 matrix, vectors and SpMV accumulation, stopped at
 // an inner reduction inner_tol, then x += ||r|| d in FP64. The true residual, the refinement
 // update and the convergence test stay FP64; the inner dot products accumulate in FP64. A system
 // whose refinement step fails to halve the FP64 residual (complex64 COCG stalls on strongly
-// indefinite systems) continues as FP64 COCG from its current iterate in the same launch; an
-// inner solve that did not reduce its own residual contributes no correction.
+// indefinite systems) is restarted as FP64 COCG from x = 0 in the same launch; an inner solve
+// that did not reduce its own residual contributes no correction.
 //
 // Matrices are stored slot-major (27 values per row, val[k * n + row], columns implicit from
 // the lattice offsets), one thread per row.
@@ -75,8 +76,9 @@ struct KState {
   int discard;   // mixed: the inner solve did not reduce its residual; skip its correction
   int fell_back; // mixed: the system finished in FP64 COCG
   int reset_x;   // mixed: the fallback restarts from x = 0 (refinement left x worse than zero)
+  int best_it;   // step of the last halving of the best residual estimate
   unsigned arrive;
-  double bnorm, rnorm, relres, est, prev_rel;
+  double bnorm, rnorm, relres, est, prev_rel, best_est;
   cd rho, alpha, beta;
 };
 
@@ -104,6 +106,7 @@ struct KParams {
   int inner_maxit;
   int max_outer;
   int max_steps;
+  int stall;
 };
 
 
@@ -256,6 +259,8 @@ __device__ void init_tile(const KParams& P, int t, double* sh, bool mixed) {
       S->amode = 1;
       S->mode = MODE_RESID;
       S->prev_rel = 1.0;
+      S->best_est = 1.0;
+      S->best_it = 0;
       if (S->bnorm == 0.0) finish(P, S, HELM_OK, 0.0);
     }
   }
@@ -348,8 +353,12 @@ __device__ void phaseB_fp64(const KParams& P, int t, double* sh) {
       const double est = sqrt(rr.re) / S->bnorm;
       S->est = est;
       S->amode = 0;
-      if (!(est > P.tol) || S->it >= P.maxit || S->bd) {
-        S->cmode = C_CHECK;
+      if (est < 0.5 * S->best_est) {
+        S->best_est = est;
+        S->best_it = S->it;
+      }
+      if (!(est > P.tol) || S->it >= P.maxit || S->bd || (P.stall > 0 && S->it - S->best_it >= P.stall)) {
+        S->cmode = C_CHECK;  // converged estimate, step cap, breakdown, or stagnation: true residual
       } else {
         S->beta = cdiv(rho_new, S->rho);
         S->rho = rho_new;
@@ -425,6 +434,8 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
         S->rho = rho;
         S->amode = 1;
         S->restarts += 1;
+        S->best_est = rel;
+        S->best_it = S->it;
       }
     }
   }
@@ -473,10 +484,13 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
         else if (!(rel == rel)) { S->pend = 1; S->status = HELM_NAN; }
         else if (S->outer >= P.max_outer || S->it >= P.maxit) { S->pend = 1; S->status = HELM_NOT_CONVERGED; }
         else if (S->outer >= 1 && rel > 0.5 * S->prev_rel) {
-          // complex64 refinement stalls on this system: continue with FP64 COCG from x, or
-          // from x = 0 if the refinement left x worse than zero (phase B then sets r = b)
+          // complex64 refinement stalls on this system: restart it as FP64 COCG from x = 0
+          // (phase B sets x = 0, r = b). COCG's path on these indefinite systems depends on its
+          // starting vector; from zero the fallback runs exactly the plain FP64 iteration.
           S->to_fp64 = 1;
-          S->reset_x = rel > 1.0;
+          S->reset_x = 1;
+          S->best_est = 1.0;
+          S->best_it = S->it;
           S->rho = rho;
           S->amode = 1;
           S->bd = 0;
@@ -881,6 +895,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   P.inner_tol = o.inner_tol;
   P.inner_maxit = o.inner_maxit;
   P.max_outer = o.max_outer;
+  P.stall = o.stall_window;
   // each super-step advances every active system by one Krylov step, except refinement
   // residual steps (at most max_outer + 1 of them) and COCG residual checks
   P.max_steps = 2 * o.maxit + 2 * (o.max_outer + 2) + 16;

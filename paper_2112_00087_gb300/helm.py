@@ -51,7 +51,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("restart", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int32), ("precond", ctypes.c_int32), ("ras_parts", ctypes.c_int32 * 3),
                 ("ras_overlap", ctypes.c_int32), ("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("inner_maxit", ctypes.c_int32), ("max_outer", ctypes.c_int32)]
+                ("inner_maxit", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("stall_window", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):
@@ -130,7 +131,7 @@ def _stream(stream=None):
 
 
 def make_opts(solver="cocg", restart=50, tol=1e-10, maxit=100000, precond=None, ras_parts=(8, 4, 4),
-              ras_overlap=2, mixed=False, inner_tol=1e-4, inner_maxit=5000, max_outer=50) -> SolveOpts:
+              ras_overlap=2, mixed=False, inner_tol=1e-4, inner_maxit=5000, max_outer=50, stall_window=0) -> SolveOpts:
     o = SolveOpts()
     o.solver = HELM_SOLVER_GMRES if solver == "gmres" else HELM_SOLVER_COCG
     o.restart = restart
@@ -143,6 +144,7 @@ def make_opts(solver="cocg", restart=50, tol=1e-10, maxit=100000, precond=None, 
     o.inner_tol = inner_tol
     o.inner_maxit = inner_maxit
     o.max_outer = max_outer
+    o.stall_window = stall_window
     return o
 
 
