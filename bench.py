@@ -38,6 +38,27 @@ METRIC = "FRF freqs/s at rel-res 1e-10: batched+mixed vs plain FP64; SpMV % HBM 
 TOL = 1e-10
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent launch of the
+# default benchmark step, from a single-pass ncu capture (profiles/traffic_sweep256.md), valid
+# only for the kernel sources it was taken on: reported as null once they change.
+TRAFFIC_CAPTURE = {"sources_sha256_16": "c0be1ff6bd7b1166", "bytes": 98444236640512 + 10995534523904}
+KERNEL_SOURCES = ("paper_2112_00087_gb300/csrc/krylov_cocg.cu", "paper_2112_00087_gb300/csrc/kernels.cuh",
+                  "paper_2112_00087_gb300/csrc/common.cuh")
+
+
+def captured_traffic(args):
+    if args.traffic is not None:
+        return args.traffic
+    if args.workload != "sweep256" or args.nfreq != 256 or args.mixed:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC_CAPTURE["bytes"] if h.hexdigest()[:16] == TRAFFIC_CAPTURE["sources_sha256_16"] else None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -65,6 +86,17 @@ def cocg_fp64_bytes(n, nnz, st):
     per_it = dia_spmv_bytes(n, 16) + 96 * n + 48 * n      # SpMV, x/r update, p update
     check = dia_spmv_bytes(n, 16) + 32 * n                # b read, r written
     return it * per_it + chk * check + 48 * n             # + init (b read, x and r written)
+
+
+# FP64 flops per row of one FP64 COCG step: 27 complex-by-real stencil products (4 flops each),
+# the p^T q and r^T r / ||r||^2 dot products, the x, r and p updates -- 152 in total.
+FP64_FLOPS_PER_ROW_STEP = 27 * 4 + 8 + 8 + 8 + 8 + 4 + 8
+# GB300 FP64: 2 FMA per SM per clock x 152 SMs x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def cocg_fp64_flops(n, st):
+    return (st["iterations"] - st.get("iterations_c64", 0)) * n * FP64_FLOPS_PER_ROW_STEP
 
 
 def cocg_mixed_bytes(n, nnz, st):
@@ -152,12 +184,19 @@ def build_sweep(nfreq, helm, torch, workload="sweep256"):
     return freqs, probs, ctxs, outs
 
 
-def mixed_opts(helm, maxit=400000):
-    return helm.make_opts("cocg", tol=TOL, maxit=maxit, mixed=True, inner_tol=1e-4, inner_maxit=600, max_outer=40)
+# COCG stagnation window: longer than any plateau of a system that converges without a restart
+# (the longest sweep system, 500 Hz, converges in about 13,500 steps), so the rule only touches
+# systems that are genuinely stuck (374 Hz sits near rel-res 1e-2 without it).
+STALL = 15000
 
 
-def fp64_opts(helm, maxit=400000):
-    return helm.make_opts("cocg", tol=TOL, maxit=maxit)
+def mixed_opts(helm, maxit=45000):
+    return helm.make_opts("cocg", tol=TOL, maxit=maxit, mixed=True, inner_tol=1e-4, inner_maxit=600, max_outer=40,
+                          stall_window=STALL)
+
+
+def fp64_opts(helm, maxit=45000):
+    return helm.make_opts("cocg", tol=TOL, maxit=maxit, stall_window=STALL)
 
 
 def timed(fn, torch, K, W, dist=None):
@@ -294,6 +333,21 @@ def run_gpu(args):
     kern_s = prof["solve_ms"] / 1e3
     achieved = alg / kern_s / 1e9
     launches = sum(p["launches"] for _, p in results)
+    traffic = captured_traffic(args)
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
+           "traffic": traffic, "kernel": "cocg_persistent<%s>" % ("mixed" if main_mixed else "fp64"),
+           "algorithmic_bytes": alg, "kernel_ms": prof["solve_ms"], "peak_kind": peak_kind}
+    if main_mixed:
+        roof = hbm
+    else:
+        # the FP64 step is bound by the FP64 pipe on GB300: report that roofline, HBM beside it
+        fl = sum(cocg_fp64_flops(c.n, s) for c, s in zip(ctxs, stats))
+        tf = fl / kern_s / 1e12
+        roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "cocg_persistent<fp64>", "algorithmic_flops": fl, "kernel_ms": prof["solve_ms"],
+                "peak_kind": "derived: FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "algorithmic_bytes", "peak_kind")}}
     desc = ("sweep256: %d log-spaced frequencies 20-500 Hz, each on its own wavelength-scaled 2.5x1.4x1.2 m "
             "cabin lattice (24x14x12..148x83x71, %d nodes total), sun-roof Dirichlet pressure + random seat "
             "admittance; assembly + lifting + COCG to true rel-res 1e-10 for all systems in one persistent "
@@ -313,10 +367,7 @@ def run_gpu(args):
                           "max": int(max(s["iterations"] for s in stats)),
                           "relres_max": max(s["relres"] for s in stats)},
            "phases_ms": {"assemble": prof["assemble_ms"], "solve": prof["solve_ms"]},
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                        "frac": achieved / peak_gbs, "traffic": None,
-                        "kernel": "cocg_persistent<%s>" % ("mixed" if main_mixed else "fp64"),
-                        "algorithmic_bytes": alg, "kernel_ms": prof["solve_ms"], "peak_kind": peak_kind},
+           "roofline": roof,
            "gpu_launches": int(launches), "clocks": clk}
 
     if rank == 0 and not args.quick:
@@ -376,6 +427,85 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_configs(args):
+    """Secondary workloads (not the benchmark line): one JSON object with their measurements."""
+    import torch
+    from paper_2112_00087_gb300 import helm
+
+    def ctx_of(pr):
+        m = pr.mesh
+        c = helm.Context(m.nx, m.ny, m.nz, m.Lx, m.Ly, m.Lz)
+        c.set_boundary(torch.from_numpy(pr.beta).cuda(), torch.from_numpy(pr.dir_nodes).cuda(),
+                       torch.from_numpy(pr.p_dir).cuda())
+        return c
+
+    def run(c, freqs, o):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p, st = helm.helm_solve(c, freqs, o, raise_on_fail=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        pr_ = helm.helm_last_profile()
+        return p, st, dt, pr_
+
+    res = {}
+    # box100: GMRES(30) and COCG, FP64, 100 Hz
+    c = ctx_of(hi.small_box_problem())
+    out = {}
+    for name, o in (("gmres30", helm.make_opts("gmres", restart=30, tol=TOL, maxit=20000)),
+                    ("cocg", helm.make_opts("cocg", tol=TOL, maxit=20000))):
+        run(c, [100.0], o)
+        _, st, dt, pr_ = run(c, [100.0], o)
+        out[name] = {"ms": dt * 1e3, "solve_ms": pr_["solve_ms"], "iterations": st[0]["iterations"],
+                     "restarts": st[0]["restarts"], "relres": st[0]["relres"], "status": st[0]["status"]}
+    res["box100"] = out
+    # cabin282k: GMRES(50) + RAS 8x4x4 overlap 2 at 20/100/200 Hz, and COCG for comparison
+    c = ctx_of(hi.cabin_problem(100, 56, 48))
+    out = {}
+    for f in (20.0, 100.0, 200.0):
+        o = helm.make_opts("gmres", restart=50, tol=TOL, maxit=5000, precond="ras", ras_parts=(8, 4, 4), ras_overlap=2)
+        _, st, dt, pr_ = run(c, [f], o)
+        o2 = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
+        _, st2, dt2, pr2 = run(c, [f], o2)
+        out["%g" % f] = {"ras_gmres50": {"ms_total": dt * 1e3, "solve_ms": pr_["solve_ms"],
+                                         "iterations": st[0]["iterations"], "relres": st[0]["relres"],
+                                         "status": st[0]["status"]},
+                         "cocg": {"ms_total": dt2 * 1e3, "iterations": st2[0]["iterations"],
+                                  "relres": st2[0]["relres"], "status": st2[0]["status"]}}
+    res["cabin282k"] = out
+    # cabin2m: every 8th of the 32 frequencies, FP64 vs mixed, batched per precision
+    pr = hi.cabin_problem(200, 112, 96)
+    c = ctx_of(pr)
+    fr = list(np.geomspace(100.0, 400.0, 32)[::8])
+    p64, st64, dt64, _ = run(c, fr, helm.make_opts("cocg", tol=TOL, maxit=60000, stall_window=STALL))
+    pmx, stmx, dtmx, _ = run(c, fr, mixed_opts(helm, 60000))
+    err = [float((torch.linalg.norm(pmx[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
+    res["cabin2m_sample"] = {"freqs": [float(f) for f in fr], "n": c.n,
+                             "fp64": {"freqs_per_s": len(fr) / dt64, "iterations": [s_["iterations"] for s_ in st64],
+                                      "status": [s_["status"] for s_ in st64]},
+                             "mixed": {"freqs_per_s": len(fr) / dtmx, "iterations": [s_["iterations"] for s_ in stmx],
+                                       "c64": [s_["iterations_c64"] for s_ in stmx], "outer": [s_["outer"] for s_ in stmx],
+                                       "status": [s_["status"] for s_ in stmx]},
+                             "rel_l2_mixed_vs_fp64": err}
+    del p64, pmx
+    # adjoint64: 64 frequencies 20-300 Hz on the 282k cabin, forward + adjoint
+    pr = hi.cabin_problem(100, 56, 48)
+    c = ctx_of(pr)
+    fr = list(np.geomspace(20.0, 300.0, 64))
+    o = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
+    p, st, dtf, _ = run(c, fr, o)
+    w = torch.from_numpy(hi.listener_weights(pr.mesh)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, gb, gd = helm.helm_adjoint_grad(c, fr, o, p, w)
+    torch.cuda.synchronize()
+    dta = time.perf_counter() - t0
+    res["adjoint64"] = {"forward_s": dtf, "adjoint_s": dta, "ms_per_frequency_forward_plus_adjoint": (dtf + dta) / 64 * 1e3,
+                        "J": J, "converged_forward": sum(1 for s_ in st if s_["status"] == 0),
+                        "grad_beta_norm": float(torch.linalg.norm(gb).item()), "n_seat_faces": int((torch.from_numpy(pr.beta) != 0).sum())}
+    print(json.dumps({"configs": res}), flush=True)
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -413,13 +543,18 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--workload", default="sweep256", choices=["sweep256", "cabin2m", "cabin282k"],
                     help="sweep256 is the benchmark; the one-lattice cases serve profiling")
-    ap.add_argument("--maxit", type=int, default=30000, help="Krylov step cap per system")
+    ap.add_argument("--maxit", type=int, default=45000, help="Krylov step cap per system")
     ap.add_argument("--mixed", action="store_true", help="time the mixed-precision solver as the main leg")
     ap.add_argument("--fp64", action="store_true", help="(default) time the FP64 solver as the main leg")
     ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
+    ap.add_argument("--configs", action="store_true", help="measure the secondary workloads instead")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes (read + write) of one persistent launch from an ncu capture, if known")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.configs:
+        run_configs(args)
     else:
         run_gpu(args)
 

@@ -123,3 +123,14 @@ def test_ras_gmres_solution_equals_direct():
     assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
     _, st0 = krylov.gmres(lambda v: A @ v, b, 30, tol=1e-11)
     assert st.iterations < st0.iterations
+
+
+def test_cocg_stagnation_restart_reaches_the_same_solution():
+    # a restarted COCG (short stagnation window, so it restarts many times) still converges to the
+    # dense-LU solution; the restarts are counted
+    prob = hi.small_box_problem(6, 4, 3)
+    A, b = fem.system(prob, 230.0)
+    ref = np.linalg.solve(A.toarray(), b)
+    x, st = krylov.cocg(lambda v: A @ v, b, tol=1e-12, maxit=20000, stall=20)
+    assert st.converged and st.restarts > 0
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
