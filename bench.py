@@ -199,6 +199,21 @@ def fp64_opts(helm, maxit=45000):
     return helm.make_opts("cocg", tol=TOL, maxit=maxit, stall_window=STALL)
 
 
+def max_over_ranks(secs, dist, device):
+    """Slowest rank's time (the benchmark's value divides every rank's work by it)."""
+    if dist is None:
+        return secs
+    import torch
+    t = torch.tensor([float(secs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(world, units_per_rank, steps, secs):
+    """Whole-job throughput: the units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank * steps / secs
+
+
 def timed(fn, torch, K, W, dist=None):
     for _ in range(W):
         fn()
@@ -320,13 +335,10 @@ def run_gpu(args):
     clocks.start()
     secs, wall, results = timed(step, torch, args.steps, 0, dist)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = t.item()
+    secs = max_over_ranks(secs, dist, "cuda")
     stats, prof = results[-1]
     n_ok = sum(1 for s in stats if s["status"] == 0)
-    value = world * nsys * args.steps / secs
+    value = job_value(world, nsys, args.steps, secs)
 
     # roofline of the dominant kernel (the persistent solve), from the last timed step
     alg = sum(bytes_fn(c.n, c.nnz, s) for c, s in zip(ctxs, stats))

@@ -1,6 +1,7 @@
 // extern "C" entry points of libhelm (declared and documented in include/helm.h).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -14,6 +15,14 @@ static thread_local std::string g_err;
 static thread_local helm_profile g_prof;
 
 helm_profile& last_profile() { return g_prof; }
+
+FaultMode fault_mode() {
+  const char* e = getenv("HELM_FAULT_INJECT");
+  if (!e) return FAULT_NONE;
+  if (strcmp(e, "barrier") == 0) return FAULT_BARRIER;
+  if (strcmp(e, "oom") == 0) return FAULT_OOM;
+  return FAULT_NONE;
+}
 
 helm_status set_error(helm_status st, const std::string& msg) {
   g_err = msg;

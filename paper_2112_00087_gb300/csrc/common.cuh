@@ -152,11 +152,21 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
 helm_status adjoint_grad(helm_ctx* ctx, const double* freqs, int nfreq, const helm_solve_opts& o,
                          const cd* p, const double* w, const cd* gp, cd* grad_beta, cd* grad_pdir, double* J);
 
+// Host-side fault injection for the failure-detection tests, read from the environment
+// variable HELM_FAULT_INJECT: "barrier" (persistent solver barriers wait for a block that does
+// not exist and time out after 200 ms) or "oom" (the next device allocation of the library
+// reports out-of-memory). Unset in normal use; nothing here can fault the GPU.
+enum FaultMode { FAULT_NONE = 0, FAULT_BARRIER = 1, FAULT_OOM = 2 };
+FaultMode fault_mode();
+
 // alloc helper: cudaMalloc with OOM mapping
 template <typename T>
 helm_status dev_alloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return HELM_OK;
+  if (fault_mode() == FAULT_OOM)
+    return set_error(HELM_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) +
+                                       " bytes failed (injected)");
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();

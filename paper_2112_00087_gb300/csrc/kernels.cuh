@@ -222,7 +222,10 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks) {
+// `extra` adds arrivals the barrier waits for (0 in normal operation; the fault-injection test
+// sets 1, so no generation bump ever happens and every block gives up after `timeout_ns`).
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks, unsigned extra = 0,
+                                             unsigned long long timeout_ns = kTimeoutNs) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -230,7 +233,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks) {
     const unsigned g = ld_acquire(&bar->gen);
     __threadfence();
     const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
-    if (arrived == nblocks) {
+    if (arrived == nblocks + extra) {
       atomicExch(&bar->count, 0u);
       __threadfence();
       atomicAdd(&bar->gen, 1u);
@@ -239,7 +242,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks) {
       unsigned spins = 0;
       while (ld_acquire(&bar->gen) == g) {
         ++spins;
-        if (spins > kSpinLimit || ((spins & 1023u) == 0 && globaltimer() - t0 > kTimeoutNs)) {
+        if (spins > kSpinLimit || ((spins & 1023u) == 0 && globaltimer() - t0 > timeout_ns)) {
           atomicOr(&bar->status, DEV_TIMEOUT);
           ok = 0;
           break;

@@ -107,6 +107,8 @@ struct KParams {
   int max_outer;
   int max_steps;
   int stall;
+  unsigned bar_extra;             // fault injection: arrivals the barriers wait for in addition
+  unsigned long long bar_timeout;  // barrier give-up time (ns)
 };
 
 
@@ -716,7 +718,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
   const unsigned nb = gridDim.x;
   int seen_fin = 0;
   for (int t = blockIdx.x; t < P.ntiles; t += nb) init_tile(P, t, sh, MIXED);
-  if (!grid_barrier(P.bar, nb)) return;
+  if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
   for (int step = 0; step < P.max_steps; ++step) {
     if (vload(&P.ctrl[CTRL_NACT]) == 0) break;
     const int cur = vload(&P.ctrl[CTRL_CUR]);
@@ -728,18 +730,18 @@ __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
       if (MIXED && !in_fp64(P, list[a])) phaseA_mixed(P, list[a], sh);
       else phaseA_fp64(P, list[a], sh);
     }
-    if (!grid_barrier(P.bar, nb)) return;
+    if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
     if (rebuilt && threadIdx.x == 0) P.ctrl[CTRL_CUR] = cur ^ 1;
     for (int a = blockIdx.x; a < nat; a += nb) {
       if (MIXED && !in_fp64(P, list[a])) phaseB_mixed(P, list[a], sh);
       else phaseB_fp64(P, list[a], sh);
     }
-    if (!grid_barrier(P.bar, nb)) return;
+    if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
     for (int a = blockIdx.x; a < nat; a += nb) {
       if (MIXED && !in_fp64(P, list[a])) phaseC_mixed(P, list[a], sh);
       else phaseC_fp64(P, list[a], sh);
     }
-    if (!grid_barrier(P.bar, nb)) return;
+    if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
   }
 }
 
@@ -896,6 +898,12 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   P.inner_maxit = o.inner_maxit;
   P.max_outer = o.max_outer;
   P.stall = o.stall_window;
+  // Host-side fault injection for tests (never set in normal use): the barriers wait for one
+  // block that does not exist and give up after 200 ms, so the launch ends with HELM_TIMEOUT
+  // without faulting or hanging the GPU.
+  const FaultMode fm = fault_mode();
+  P.bar_extra = fm == FAULT_BARRIER ? 1u : 0u;
+  P.bar_timeout = fm == FAULT_BARRIER ? 200000000ull : kTimeoutNs;
   // each super-step advances every active system by one Krylov step, except refinement
   // residual steps (at most max_outer + 1 of them) and COCG residual checks
   P.max_steps = 2 * o.maxit + 2 * (o.max_outer + 2) + 16;
