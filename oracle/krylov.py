@@ -18,6 +18,14 @@ by step in complex128 numpy, the two iterations the GPU path runs:
   x with r = b - A x. Optional stagnation rule (``stall``): when the estimate has not halved
   its best value within ``stall`` steps, the same check-and-restart is taken.
 
+* ``bicgstab``: BiCGSTAB (van der Vorst 1992), the paper's own Sec. 4 solver (Table 3,
+  "P-BiCGSTAB"; the paper does not name its preconditioner "P", so none is applied), complex
+  form with Hermitian inner products (u, v) = v^H u and shadow residual r0* = r0:
+  alpha = (r, r0*)/(A p, r0*), s = r - alpha A p, omega = (A s, s)/(A s, A s),
+  x += alpha p + omega s, r = s - omega A s, beta = (r_new, r0*)/(r, r0*) * alpha/omega,
+  p = r + beta (p - omega A p); stop on ||r||/||b|| <= tol, confirm with the true residual,
+  restart from x if it misses. One iteration = two products with A.
+
 Iteration count = number of Krylov steps (products with A inside the iteration; the
 true-residual products are not counted).
 
@@ -191,3 +199,54 @@ def cocg(matvec, b, tol=1e-10, maxit=100000, stall=None):
             return x, st
         st.restarts += 1
         best, best_it = st.relres, st.iterations
+
+
+def bicgstab(matvec, b, tol=1e-10, maxit=100000):
+    """BiCGSTAB for general complex A. Returns (x, Stats); Stats.iterations counts iterations
+    (two products with A each)."""
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128)
+    st = Stats()
+    nb = nrm2(b)
+    if nb == 0:
+        st.converged, st.relres = True, 0.0
+        return x, st
+    r = b.copy()
+    while True:
+        rs = r.copy()           # shadow residual r0*
+        p = r.copy()
+        rho = dotc(rs, r)       # (r, r0*) = r0*^H r
+        while st.iterations < maxit:
+            v = matvec(p)
+            st.iterations += 1
+            den = dotc(rs, v)
+            if den == 0 or rho == 0:
+                st.breakdown = True
+                break
+            alpha = rho / den
+            s_ = r - alpha * v
+            t = matvec(s_)
+            tt = dotc(t, t).real
+            omega = dotc(t, s_) / tt if tt != 0 else 0.0
+            x = x + alpha * p + omega * s_
+            r = s_ - omega * t
+            est = nrm2(r) / nb
+            st.history.append(est)
+            if est <= tol:
+                break
+            if omega == 0:
+                st.breakdown = True
+                break
+            rho_new = dotc(rs, r)
+            beta = (rho_new / rho) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+            rho = rho_new
+        r = b - matvec(x)
+        st.relres = nrm2(r) / nb
+        if st.relres <= tol:
+            st.converged = True
+            return x, st
+        if st.iterations >= maxit or st.breakdown:
+            return x, st
+        st.restarts += 1

@@ -134,3 +134,26 @@ def test_cocg_stagnation_restart_reaches_the_same_solution():
     x, st = krylov.cocg(lambda v: A @ v, b, tol=1e-12, maxit=20000, stall=20)
     assert st.converged and st.restarts > 0
     assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("dims,f", [((3, 2, 2), 150.0), ((6, 4, 3), 230.0), ((10, 8, 6), 100.0)])
+def test_bicgstab_matches_dense_lu(dims, f):
+    prob = hi.small_box_problem(*dims)
+    A, b = fem.system(prob, f)
+    ref = np.linalg.solve(A.toarray(), b)
+    x, st = krylov.bicgstab(lambda v: A @ v, b, tol=1e-12)
+    assert st.converged
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_bicgstab_on_nonsymmetric_system_and_real_spd():
+    # BiCGSTAB needs no symmetry: a random complex nonsymmetric, diagonally dominant system
+    rng = np.random.default_rng(2)
+    n = 30
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 12 * np.eye(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, st = krylov.bicgstab(lambda v: A @ v, b, tol=1e-13)
+    assert st.converged and np.allclose(x, np.linalg.solve(A, b), rtol=1e-11)
+    # on a 1x1 system it converges in one iteration
+    x1, st1 = krylov.bicgstab(lambda v: 3.0 * v, np.array([2.0 + 1j]), tol=1e-14)
+    assert st1.converged and st1.iterations == 1 and abs(x1[0] - (2.0 + 1j) / 3.0) < 1e-15
