@@ -26,6 +26,17 @@ by step in complex128 numpy, the two iterations the GPU path runs:
   p = r + beta (p - omega A p); stop on ||r||/||b|| <= tol, confirm with the true residual,
   restart from x if it misses. One iteration = two products with A.
 
+* ``tfqmr``: transpose-free QMR (Freund 1993; as stated in Saad 2nd ed. Sec. 7.4.3), the
+  paper's other Sec. 4 solver ("P-tfQMR"), complex form with (u, v) = v^H u and r0* = r0.
+  Steps m = 0, 1, 2, ...: alpha is renewed on even steps from (r0*, v); every step updates
+  w -= alpha A u, the direction d = u + (theta^2/alpha) eta d, theta = ||w||/tau,
+  c = 1/sqrt(1 + theta^2), tau = tau theta c, eta = c^2 alpha, x += eta d; odd steps renew
+  rho = (w, r0*), beta, u = w + beta u and v = A u + beta (A u_old + beta v). The bound
+  ||r_m|| <= tau sqrt(m + 1) is the stopping estimate; then the true residual decides, and a
+  miss restarts from x. Iteration count = steps m (one product with A per step on average).
+* ``right_jacobi``: the "P" of the paper's P-BiCGSTAB / P-TFQMR read as Jacobi, applied on the
+  right (A D^-1 y = b, x = D^-1 y, D = diag(A)), so residuals stay those of A x = b.
+
 Iteration count = number of Krylov steps (products with A inside the iteration; the
 true-residual products are not counted).
 
@@ -250,3 +261,80 @@ def bicgstab(matvec, b, tol=1e-10, maxit=100000):
         if st.iterations >= maxit or st.breakdown:
             return x, st
         st.restarts += 1
+
+
+def tfqmr(matvec, b, tol=1e-10, maxit=100000):
+    """Transpose-free QMR for general complex A. Returns (x, Stats); Stats.iterations counts
+    steps m."""
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128)
+    st = Stats()
+    nb = nrm2(b)
+    if nb == 0:
+        st.converged, st.relres = True, 0.0
+        return x, st
+    r = b.copy()
+    while True:
+        rs = r.copy()                   # r0*
+        w = r.copy()
+        u = r.copy()
+        v = matvec(u)
+        au = v                          # A u for the current u
+        d = np.zeros(n, dtype=np.complex128)
+        tau = nrm2(r)
+        theta, eta = 0.0, 0.0 + 0.0j
+        rho = dotc(rs, r)
+        alpha = 0.0 + 0.0j
+        m = 0
+        while st.iterations < maxit:
+            if m % 2 == 0:
+                den = dotc(rs, v)
+                if den == 0 or rho == 0:
+                    st.breakdown = True
+                    break
+                alpha = rho / den
+                u_next = u - alpha * v
+            else:
+                au = matvec(u)
+            st.iterations += 1
+            w = w - alpha * au
+            d = u + (theta * theta / alpha) * eta * d
+            theta = nrm2(w) / tau
+            c = 1.0 / np.sqrt(1.0 + theta * theta)
+            tau = tau * theta * c
+            eta = c * c * alpha
+            x = x + eta * d
+            est = tau * np.sqrt(m + 1.0) / nb
+            st.history.append(est)
+            if est <= tol:
+                break
+            if m % 2 == 0:
+                u = u_next
+                au = None
+            else:
+                rho_new = dotc(rs, w)
+                if rho == 0:
+                    st.breakdown = True
+                    break
+                beta = rho_new / rho
+                au_old = au
+                u = w + beta * u
+                au = matvec(u)
+                v = au + beta * (au_old + beta * v)
+                rho = rho_new
+            m += 1
+        r = b - matvec(x)
+        st.relres = nrm2(r) / nb
+        if st.relres <= tol:
+            st.converged = True
+            return x, st
+        if st.iterations >= maxit or st.breakdown:
+            return x, st
+        st.restarts += 1
+
+
+def right_jacobi(A):
+    """Right Jacobi preconditioning of a sparse matrix: returns (matvec of A D^-1, map y -> D^-1 y)."""
+    d = np.asarray(A.diagonal(), dtype=np.complex128)
+    return (lambda u: A @ (u / d)), (lambda y: y / d)

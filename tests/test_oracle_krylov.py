@@ -157,3 +157,42 @@ def test_bicgstab_on_nonsymmetric_system_and_real_spd():
     # on a 1x1 system it converges in one iteration
     x1, st1 = krylov.bicgstab(lambda v: 3.0 * v, np.array([2.0 + 1j]), tol=1e-14)
     assert st1.converged and st1.iterations == 1 and abs(x1[0] - (2.0 + 1j) / 3.0) < 1e-15
+
+
+@pytest.mark.parametrize("dims,f", [((3, 2, 2), 150.0), ((6, 4, 3), 230.0), ((10, 8, 6), 100.0)])
+def test_jacobi_tfqmr_and_bicgstab_match_dense_lu(dims, f):
+    # P-TFQMR / P-BiCGSTAB with the Jacobi reading of "P", right-preconditioned
+    prob = hi.small_box_problem(*dims)
+    A, b = fem.system(prob, f)
+    ref = np.linalg.solve(A.toarray(), b)
+    mv, unscale = krylov.right_jacobi(A)
+    for solver in (krylov.tfqmr, krylov.bicgstab):
+        y, st = solver(mv, b, tol=1e-12, maxit=20000)
+        assert st.converged, solver.__name__
+        assert np.linalg.norm(unscale(y) - ref) <= 1e-9 * np.linalg.norm(ref)
+        # right preconditioning: the residual of A D^-1 y = b is the residual of A x = b
+        assert np.linalg.norm(b - A @ unscale(y)) <= 1e-12 * np.linalg.norm(b) * 1.01
+
+
+def test_tfqmr_quasi_residual_bounds_the_true_residual():
+    # ||b - A x_m|| <= tau_m sqrt(m + 1) at every step (Freund's bound): x_m after exactly m steps
+    # against the estimate the iteration reports for step m; a wrong tau / eta / d recurrence
+    # breaks it within a few steps
+    rng = np.random.default_rng(4)
+    n = 40
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 9 * np.eye(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for k in range(1, 25):
+        x, st = krylov.tfqmr(lambda v: A @ v, b, tol=1e-300, maxit=k)
+        assert st.iterations == k
+        true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert true <= st.history[-1] * (1 + 1e-10), (k, true, st.history[-1])
+    x, st = krylov.tfqmr(lambda v: A @ v, b, tol=1e-13)
+    assert st.converged and np.allclose(x, np.linalg.solve(A, b), rtol=1e-11)
+
+
+def test_tfqmr_one_by_one_and_zero_rhs():
+    x, st = krylov.tfqmr(lambda v: 3.0 * v, np.array([2.0 + 1j]), tol=1e-14)
+    assert st.converged and abs(x[0] - (2.0 + 1j) / 3.0) < 1e-15
+    x, st = krylov.tfqmr(lambda v: 3.0 * v, np.zeros(4, dtype=complex))
+    assert st.converged and st.iterations == 0 and not x.any()
