@@ -55,6 +55,7 @@ import dataclasses
 import math
 
 import numpy as np
+import scipy.sparse as sp
 
 
 def dotu(x, y):
@@ -167,12 +168,19 @@ def gmres(matvec, b, m, tol=1e-10, maxit=10000, precond=None, ortho="cgs2", x0=N
         st.restarts += 1
 
 
-def cocg(matvec, b, tol=1e-10, maxit=100000, stall=None):
-    """COCG for complex-symmetric A. Returns (x, Stats)."""
+def cocg(matvec, b, tol=1e-10, maxit=100000, stall=None, weights=None):
+    """COCG for complex-symmetric A. Returns (x, Stats). With ``weights`` w >= 0 every norm is
+    the weighted norm sqrt(sum_i w_i |v_i|^2) (used by the symmetric Jacobi form, where the
+    weights turn residuals of the scaled system back into residuals of the original one)."""
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
     x = np.zeros(n, dtype=np.complex128)
     st = Stats()
+    if weights is not None:
+        w = np.asarray(weights, dtype=np.float64)
+        nrm2 = lambda v: math.sqrt(math.fsum(w * (v.real * v.real + v.imag * v.imag)))  # noqa: E731
+    else:
+        nrm2 = globals()["nrm2"]
     nb = nrm2(b)
     if nb == 0:
         st.converged, st.relres = True, 0.0
@@ -338,3 +346,15 @@ def right_jacobi(A):
     """Right Jacobi preconditioning of a sparse matrix: returns (matvec of A D^-1, map y -> D^-1 y)."""
     d = np.asarray(A.diagonal(), dtype=np.complex128)
     return (lambda u: A @ (u / d)), (lambda y: y / d)
+
+
+def sym_jacobi(A):
+    """Symmetric Jacobi scaling of a complex-symmetric sparse A (the COCG reading of the paper's
+    "P"): S = diag(s), s_i = 1 / sqrt(a_ii) (principal root), A_hat = S A S stays complex
+    symmetric. A x = b is solved as A_hat y = S b, x = S y; residuals map back as r = S^-1 r_hat,
+    so ||r||^2 = sum_i |a_ii| |r_hat_i|^2: returns (A_hat, s, w) with w_i = |a_ii| the norm
+    weights that make cocg(..., weights=w) test the residual of A x = b."""
+    d = np.asarray(A.diagonal(), dtype=np.complex128)
+    s = 1.0 / np.sqrt(d)
+    S = sp.diags(s)
+    return (S @ A @ S).tocsr(), s, np.abs(d)

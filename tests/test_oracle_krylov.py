@@ -196,3 +196,30 @@ def test_tfqmr_one_by_one_and_zero_rhs():
     assert st.converged and abs(x[0] - (2.0 + 1j) / 3.0) < 1e-15
     x, st = krylov.tfqmr(lambda v: 3.0 * v, np.zeros(4, dtype=complex))
     assert st.converged and st.iterations == 0 and not x.any()
+
+
+@pytest.mark.parametrize("dims,f", [((3, 2, 2), 150.0), ((6, 4, 3), 230.0), ((10, 8, 6), 100.0)])
+def test_sym_jacobi_cocg_matches_dense_lu(dims, f):
+    prob = hi.small_box_problem(*dims)
+    A, b = fem.system(prob, f)
+    ref = np.linalg.solve(A.toarray(), b)
+    Ah, s, w = krylov.sym_jacobi(A)
+    # the scaled matrix stays complex symmetric (to rounding of the two products)
+    assert abs(Ah - Ah.T).max() <= 1e-15 * abs(Ah).max()
+    y, st = krylov.cocg(lambda v: Ah @ v, s * b, tol=1e-12, weights=w)
+    x = s * y
+    assert st.converged
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+    # the weighted residual the iteration reports is the residual of the original system
+    true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert abs(st.relres - true) <= 1e-6 * true + 1e-18
+    # and its weighted right-hand-side norm is ||b||
+    assert abs(np.sqrt(np.sum(w * np.abs(s * b) ** 2)) - np.linalg.norm(b)) <= 1e-14 * np.linalg.norm(b)
+
+
+def test_weighted_norm_cocg_with_unit_weights_is_plain_cocg():
+    prob = hi.small_box_problem(6, 4, 3)
+    A, b = fem.system(prob, 230.0)
+    x1, s1 = krylov.cocg(lambda v: A @ v, b, tol=1e-10)
+    x2, s2 = krylov.cocg(lambda v: A @ v, b, tol=1e-10, weights=np.ones(len(b)))
+    assert s1.iterations == s2.iterations and np.array_equal(x1, x2)
