@@ -49,7 +49,8 @@ KERNEL_SOURCES = ("paper_2112_00087_gb300/csrc/krylov_cocg.cu", "paper_2112_0008
 def captured_traffic(args):
     if args.traffic is not None:
         return args.traffic
-    if args.workload != "sweep256" or args.nfreq != 256 or args.mixed:
+    if (args.workload != "sweep256" or args.nfreq != 256 or args.mixed or args.solver != "cocg"
+            or args.precision != "fp64" or args.precond != "none"):
         return None
     import hashlib
     h = hashlib.sha256()
@@ -77,8 +78,9 @@ def spmv_bytes(n, nnz, vb):
 
 
 def dia_spmv_bytes(n, vb):
-    """Slot-major 27-point SpMV: 27 n stored values + x read once + y written once."""
-    return 27 * n * vb + 2 * vb * n
+    """Slot-major split-layout SpMV: 27 n real parts (vb/2 bytes each) + x read once + y written
+    once (the imaginary parts, read only for rows next to admittance walls, are not counted)."""
+    return 27 * n * (vb // 2) + 2 * vb * n
 
 
 def cocg_fp64_bytes(n, nnz, st):
@@ -97,6 +99,49 @@ FP64_PEAK_TFLOPS = 1.25
 
 def cocg_fp64_flops(n, st):
     return (st["iterations"] - st.get("iterations_c64", 0)) * n * FP64_FLOPS_PER_ROW_STEP
+
+
+def bicgstab_bytes(n, nnz, st):
+    """FP64 BiCGSTAB: per iteration two SpMVs (v = A p, t = A s) and 240 n bytes of vector
+    traffic -- rs read (16), s = r - alpha v (48), x/r updates and rs^H r (112), p update (64)."""
+    it, chk = st["iterations"], st["restarts"] + 1
+    return it * (2 * dia_spmv_bytes(n, 16) + 240 * n) + chk * (dia_spmv_bytes(n, 16) + 32 * n) + 48 * n
+
+
+def cocg_dw_bytes(n, nnz, st):
+    """Double-word mixed mode: inner steps move what an FP64 step moves (matrix parts as 8-byte
+    (hi, lo) float pairs, vectors as 16-byte complex double-words), plus the FP64 refinement
+    residuals, inner starts (r read, r and d written) and corrections (d and x read, x written)."""
+    it_in, outer = st["iterations_c64"], abs(st["outer"])
+    it64 = st["iterations"] - it_in
+    step = dia_spmv_bytes(n, 16) + 96 * n + 48 * n
+    resid = dia_spmv_bytes(n, 16) + 32 * n
+    return it_in * step + it64 * step + (outer + 1) * resid + outer * (48 * n + 48 * n) + 48 * n
+
+
+def tfqmr_bytes(n, nnz, st):
+    """FP64 TFQMR, per step (half of a pair of two SpMVs): one SpMV and 208 n bytes of vector
+    traffic (a pair moves 416 n: even step 112, odd step 144, u update 96, v update 64)."""
+    it, chk = st["iterations"], st["restarts"] + 1
+    # per (re)start cycle: true residual (SpMV, b read, r written), setup (r read, w u r0* d
+    # written), first v = A u (SpMV, r0* read)
+    return it * (dia_spmv_bytes(n, 16) + 208 * n) + chk * (2 * dia_spmv_bytes(n, 16) + 32 * n + 80 * n + 16 * n) + 48 * n
+
+
+TFQMR_FLOPS_PER_ROW_STEP = (2 * 27 * 4 + 28 + 36 + 16 + 24) // 2
+
+
+def tfqmr_flops(n, st):
+    return st["iterations"] * n * TFQMR_FLOPS_PER_ROW_STEP
+
+
+# FP64 flops per row of one BiCGSTAB iteration: two stencil products (2 x 108) and 80 for the
+# rs^H v, t^H s, t^H t, rs^H r, ||r||^2 dots and the s, x, r, p updates.
+BICG_FLOPS_PER_ROW_IT = 2 * 27 * 4 + 8 + 8 + 8 + 4 + 16 + 8 + 8 + 4 + 16
+
+
+def bicgstab_flops(n, st):
+    return st["iterations"] * n * BICG_FLOPS_PER_ROW_IT
 
 
 def cocg_mixed_bytes(n, nnz, st):
@@ -190,13 +235,27 @@ def build_sweep(nfreq, helm, torch, workload="sweep256"):
 STALL = 15000
 
 
-def mixed_opts(helm, maxit=45000):
+def mixed_opts(helm, maxit=45000, precond=None):
     return helm.make_opts("cocg", tol=TOL, maxit=maxit, mixed=True, inner_tol=1e-4, inner_maxit=600, max_outer=40,
-                          stall_window=STALL)
+                          stall_window=STALL, precond=precond)
 
 
-def fp64_opts(helm, maxit=45000):
-    return helm.make_opts("cocg", tol=TOL, maxit=maxit, stall_window=STALL)
+def fp64_opts(helm, maxit=45000, precond=None):
+    return helm.make_opts("cocg", tol=TOL, maxit=maxit, stall_window=STALL, precond=precond)
+
+
+def dw_opts(helm, maxit=45000, precond=None):
+    # double-word inner solve straight to the outer target (inner_tol below it), FP64 refinement
+    return helm.make_opts("cocg", tol=TOL, maxit=maxit, mixed="dw", inner_tol=1e-12, inner_maxit=maxit, max_outer=20,
+                          stall_window=STALL, precond=precond)
+
+
+def bicgstab_opts(helm, maxit=45000, precond=None):
+    return helm.make_opts("bicgstab", tol=TOL, maxit=maxit, precond=precond)
+
+
+def tfqmr_opts(helm, maxit=45000, precond=None):
+    return helm.make_opts("tfqmr", tol=TOL, maxit=maxit, precond=precond)
 
 
 def max_over_ranks(secs, dist, device):
@@ -262,9 +321,9 @@ def spmv_roofline(helm, torch, peak_gbs):
             e1.record(s)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1000.0)
-        # CSR: values + columns + rowptr + x + y; DIA27: the 27 n stored values (padding
+        # CSR: values + columns + rowptr + x + y; DIA27: the 27 n stored real parts (padding
         # included, no columns) + x + y
-        b = spmv_bytes(ctx.n, ctx.nnz, vb) if fmt == helm.HELM_FMT_CSR else 27 * ctx.n * vb + 2 * vb * ctx.n
+        b = spmv_bytes(ctx.n, ctx.nnz, vb) if fmt == helm.HELM_FMT_CSR else dia_spmv_bytes(ctx.n, vb)
         best, med = min(times), statistics.median(times)
         out[name] = {"n": ctx.n, "nnz": ctx.nnz, "bytes": b, "best_ms": best * 1e3, "median_ms": med * 1e3,
                      "gbs_best": b / best / 1e9, "gbs_median": b / med / 1e9, "frac_median": b / med / 1e9 / peak_gbs}
@@ -316,11 +375,24 @@ def run_gpu(args):
 
     freqs, probs, ctxs, outs = build_sweep(args.nfreq, helm, torch, args.workload)
     nsys = len(ctxs)
-    main_mixed = args.mixed
-    mo = mixed_opts(helm, args.maxit)
-    fo = fp64_opts(helm, args.maxit)
-    main_opts = mo if main_mixed else fo
-    bytes_fn = cocg_mixed_bytes if main_mixed else cocg_fp64_bytes
+    # legs: name -> (options, algorithmic bytes, FP64 flops or None (HBM-bound), kernel, dtype, precision)
+    pc = None if args.precond == "none" else args.precond
+    pcs = "" if pc is None else ", Jacobi-preconditioned"
+    legs = {
+        "fp64": (fp64_opts(helm, args.maxit, pc), cocg_fp64_bytes, cocg_fp64_flops, "cocg_persistent<fp64>", "c128",
+                 "fp64 COCG" + pcs),
+        "c64": (mixed_opts(helm, args.maxit, pc), cocg_mixed_bytes, None, "cocg_persistent<c64 inner>",
+                "c64-inner/c128-outer", "mixed: complex64 inner COCG, FP64 refinement" + pcs),
+        "dw": (dw_opts(helm, args.maxit, pc), cocg_dw_bytes, None, "cocg_persistent<double-word inner>",
+               "dw-inner/c128-outer", "mixed: double-word (2 x FP32, ~48-bit) inner COCG, FP64 refinement" + pcs),
+        "bicgstab": (bicgstab_opts(helm, args.maxit, pc), bicgstab_bytes, bicgstab_flops, "bicg_persistent<fp64>", "c128",
+                     "fp64 BiCGSTAB" + pcs),
+        "tfqmr": (tfqmr_opts(helm, args.maxit, pc), tfqmr_bytes, tfqmr_flops, "tfqmr_persistent<fp64>", "c128",
+                  "fp64 TFQMR" + pcs),
+    }
+    leg = args.solver if args.solver != "cocg" else ("c64" if args.mixed else args.precision)
+    bicg = leg in ("bicgstab", "tfqmr")
+    main_opts, bytes_fn, flops_fn, kname, dtype, prec_desc = legs[leg]
 
     def step():
         _, st = helm.helm_solve_batch(ctxs, freqs, main_opts, outs, raise_on_fail=False)
@@ -347,29 +419,29 @@ def run_gpu(args):
     launches = sum(p["launches"] for _, p in results)
     traffic = captured_traffic(args)
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
-           "traffic": traffic, "kernel": "cocg_persistent<%s>" % ("mixed" if main_mixed else "fp64"),
+           "traffic": traffic, "kernel": kname,
            "algorithmic_bytes": alg, "kernel_ms": prof["solve_ms"], "peak_kind": peak_kind}
-    if main_mixed:
+    if flops_fn is None:
         roof = hbm
     else:
         # the FP64 step is bound by the FP64 pipe on GB300: report that roofline, HBM beside it
-        fl = sum(cocg_fp64_flops(c.n, s) for c, s in zip(ctxs, stats))
+        fl = sum(flops_fn(c.n, s) for c, s in zip(ctxs, stats))
         tf = fl / kern_s / 1e12
         roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "cocg_persistent<fp64>", "algorithmic_flops": fl, "kernel_ms": prof["solve_ms"],
+                "kernel": kname, "algorithmic_flops": fl, "kernel_ms": prof["solve_ms"],
                 "peak_kind": "derived: FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "algorithmic_bytes", "peak_kind")}}
     desc = ("sweep256: %d log-spaced frequencies 20-500 Hz, each on its own wavelength-scaled 2.5x1.4x1.2 m "
             "cabin lattice (24x14x12..148x83x71, %d nodes total), sun-roof Dirichlet pressure + random seat "
-            "admittance; assembly + lifting + COCG to true rel-res 1e-10 for all systems in one persistent "
-            "launch" % (nsys, sum(c.n for c in ctxs))) if args.workload == "sweep256" else args.workload
+            "admittance; assembly + lifting + %s to true rel-res 1e-10 for all systems in one persistent "
+            "launch" % (nsys, sum(c.n for c in ctxs), prec_desc)) if args.workload == "sweep256" else args.workload
     out = {"metric": METRIC, "value": value, "unit": "freqs/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64-inner/c128-outer" if main_mixed else "c128",
+           "scaling": "weak", "vs_baseline": None, "dtype": dtype,
            "data": "synthetic",
-           "config": {"workload": desc, "precision": "mixed (complex64 inner, FP64 refinement)" if main_mixed
-                      else "fp64 (batched; the mixed mode is reported under 'mixed')",
+           "config": {"workload": desc, "precision": prec_desc + " (the other modes, batched, under 'legs')",
+                      "solver": args.solver, "precond": args.precond,
                       "l2": "inputs larger than L2 (%.1f GB of matrix values assembled per step)" %
                             (sum(c.n * 27 * 16 for c in ctxs) / 1e9),
                       "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -383,24 +455,27 @@ def run_gpu(args):
            "gpu_launches": int(launches), "clocks": clk}
 
     if rank == 0 and not args.quick:
-        # the other precision, batched, timed once
-        other = fo if main_mixed else mo
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, st2 = helm.helm_solve_batch(ctxs, freqs, other, outs, raise_on_fail=False)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter() - t0
-        key = "plain_fp64_batched" if main_mixed else "mixed"
-        out[key] = {"freqs_per_s": nsys / t2, "converged": sum(1 for s in st2 if s["status"] == 0),
-                    "iterations_total": int(sum(s["iterations"] for s in st2)),
-                    "c64_iterations": int(sum(s["iterations_c64"] for s in st2)),
-                    "fell_back_to_fp64": int(sum(1 for s in st2 if s["outer"] < 0))}
+        # the other COCG modes, batched, timed once each
+        out["legs"] = {}
+        for name in ("fp64", "c64", "dw"):
+            if name == leg:
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st2 = helm.helm_solve_batch(ctxs, freqs, legs[name][0], outs, raise_on_fail=False)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter() - t0
+            out["legs"][name] = {"freqs_per_s": nsys / t2, "precision": legs[name][5],
+                                 "converged": sum(1 for s in st2 if s["status"] == 0),
+                                 "iterations_total": int(sum(s["iterations"] for s in st2)),
+                                 "inner_iterations": int(sum(s["iterations_c64"] for s in st2)),
+                                 "fell_back_to_fp64": int(sum(1 for s in st2 if s["outer"] < 0))}
         if not args.no_sequential:
             # plain FP64, one frequency per call (no batching)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for c, f, o in zip(ctxs, freqs, outs):
-                helm.helm_solve_batch([c], [f], fo, [o], raise_on_fail=False)
+                helm.helm_solve_batch([c], [f], legs["fp64"][0], [o], raise_on_fail=False)
             torch.cuda.synchronize()
             out["plain_fp64_sequential"] = {"freqs_per_s": nsys / (time.perf_counter() - t0)}
         out["spmv"] = spmv_roofline(helm, torch, peak_gbs)
@@ -465,7 +540,8 @@ def run_configs(args):
     c = ctx_of(hi.small_box_problem())
     out = {}
     for name, o in (("gmres30", helm.make_opts("gmres", restart=30, tol=TOL, maxit=20000)),
-                    ("cocg", helm.make_opts("cocg", tol=TOL, maxit=20000))):
+                    ("cocg", helm.make_opts("cocg", tol=TOL, maxit=20000)),
+                    ("bicgstab", helm.make_opts("bicgstab", tol=TOL, maxit=20000))):
         run(c, [100.0], o)
         _, st, dt, pr_ = run(c, [100.0], o)
         out[name] = {"ms": dt * 1e3, "solve_ms": pr_["solve_ms"], "iterations": st[0]["iterations"],
@@ -479,11 +555,14 @@ def run_configs(args):
         _, st, dt, pr_ = run(c, [f], o)
         o2 = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
         _, st2, dt2, pr2 = run(c, [f], o2)
+        _, st3, dt3, _ = run(c, [f], helm.make_opts("bicgstab", tol=TOL, maxit=40000))
         out["%g" % f] = {"ras_gmres50": {"ms_total": dt * 1e3, "solve_ms": pr_["solve_ms"],
                                          "iterations": st[0]["iterations"], "relres": st[0]["relres"],
                                          "status": st[0]["status"]},
                          "cocg": {"ms_total": dt2 * 1e3, "iterations": st2[0]["iterations"],
-                                  "relres": st2[0]["relres"], "status": st2[0]["status"]}}
+                                  "relres": st2[0]["relres"], "status": st2[0]["status"]},
+                         "bicgstab": {"ms_total": dt3 * 1e3, "iterations": st3[0]["iterations"],
+                                      "relres": st3[0]["relres"], "status": st3[0]["status"]}}
     res["cabin282k"] = out
     # cabin2m: every 8th of the 32 frequencies, FP64 vs mixed, batched per precision
     pr = hi.cabin_problem(200, 112, 96)
@@ -515,6 +594,23 @@ def run_configs(args):
     res["adjoint64"] = {"forward_s": dtf, "adjoint_s": dta, "ms_per_frequency_forward_plus_adjoint": (dtf + dta) / 64 * 1e3,
                         "J": J, "converged_forward": sum(1 for s_ in st if s_["status"] == 0),
                         "grad_beta_norm": float(torch.linalg.norm(gb).item()), "n_seat_faces": int((torch.from_numpy(pr.beta) != 0).sum())}
+    # resonance64: 64 FFT bins 2-33.5 Hz on the 282k cabin, sun-roof pressure shaped by the
+    # synthetic PSD (the solve is linear in the Dirichlet data, so each solution is the unit-pattern
+    # solution times the bin's complex amplitude); FP64 COCG and the double-word mode, batched
+    pr = hi.cabin_problem(100, 56, 48)
+    c = ctx_of(pr)
+    fr = [float(f) for f in hi.resonance_freqs(64)]
+    amp = torch.from_numpy(hi.resonance_spectrum(np.array(fr))).cuda()
+    w = torch.from_numpy(hi.listener_weights(pr.mesh)).cuda()
+    out = {"n": c.n, "freqs": [fr[0], fr[-1], len(fr)]}
+    for name, o in (("fp64", fp64_opts(helm, 40000)), ("dw", dw_opts(helm, 40000))):
+        run(c, fr, o)
+        p, st, dt, _ = run(c, fr, o)
+        level = [float((abs(amp[k]) ** 2 * (w * (p[k].abs() ** 2)).sum()).item()) for k in range(len(fr))]
+        out[name] = {"freqs_per_s": len(fr) / dt, "iterations": int(sum(s_["iterations"] for s_ in st)),
+                     "converged": sum(1 for s_ in st if s_["status"] == 0),
+                     "listener_peak_hz": fr[int(np.argmax(level))]}
+    res["resonance64"] = out
     print(json.dumps({"configs": res}), flush=True)
 
 
@@ -556,7 +652,14 @@ def main():
     ap.add_argument("--workload", default="sweep256", choices=["sweep256", "cabin2m", "cabin282k"],
                     help="sweep256 is the benchmark; the one-lattice cases serve profiling")
     ap.add_argument("--maxit", type=int, default=45000, help="Krylov step cap per system")
-    ap.add_argument("--mixed", action="store_true", help="time the mixed-precision solver as the main leg")
+    ap.add_argument("--mixed", action="store_true", help="same as --precision c64")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "c64", "dw"],
+                    help="COCG mode of the main leg: FP64, or FP64 refinement around a complex64 / double-word "
+                         "inner solve")
+    ap.add_argument("--solver", default="cocg", choices=["cocg", "bicgstab", "tfqmr"],
+                    help="Krylov method of the main leg (BiCGSTAB / TFQMR: FP64)")
+    ap.add_argument("--precond", default="none", choices=["none", "jacobi"],
+                    help="Jacobi preconditioning (symmetric for COCG, right for BiCGSTAB / TFQMR)")
     ap.add_argument("--fp64", action="store_true", help="(default) time the FP64 solver as the main leg")
     ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
     ap.add_argument("--configs", action="store_true", help="measure the secondary workloads instead")

@@ -181,6 +181,23 @@ def sweep_freqs(n: int = 256) -> np.ndarray:
     return np.geomspace(20.0, 500.0, n)
 
 
+def resonance_freqs(n: int = 64) -> np.ndarray:
+    """Frequencies of the resonance sweep: bins 4 .. 4+n-1 of a 512-point FFT sampled at 256 Hz
+    (0.5 Hz spacing, 2.0 .. 33.5 Hz for n = 64), around the compartment's 13 Hz response
+    (paper Sec. 3.1: the sun-roof spectrum peaks near 13 Hz, with a half harmonic near 6 Hz)."""
+    return 0.5 * (4 + np.arange(n))
+
+
+def resonance_spectrum(freqs: np.ndarray, seed: int = 2) -> np.ndarray:
+    """Complex amplitude of the sun-roof pressure per frequency: sqrt of a PSD shape with a
+    Lorentzian peak at 13 Hz (half width 1.5 Hz), a weaker one at 6.5 Hz (half width 1 Hz) and a
+    floor, times a seeded random phase (a PSD carries no phase)."""
+    f = np.asarray(freqs, dtype=np.float64)
+    psd = 1.0 / (1.0 + ((f - 13.0) / 1.5) ** 2) + 0.3 / (1.0 + ((f - 6.5) / 1.0) ** 2) + 0.02
+    phase = np.random.default_rng(seed).uniform(0.0, 2.0 * np.pi, f.size)
+    return np.sqrt(psd) * np.exp(1j * phase)
+
+
 def listener_weights(mesh: Mesh, centre=LISTENER_CENTRE, radius=LISTENER_RADIUS) -> np.ndarray:
     """w_i = 1/|S| for nodes within the listener sphere S, else 0 (real64 [n])."""
     n = mesh.n_nodes
@@ -213,7 +230,7 @@ class Workload:
 
 
 def workload(name: str) -> Workload:
-    """The five workloads: box100 (n=4641), cabin282k, sweep256, cabin2m, adjoint64."""
+    """The workloads: box100 (n=4641), cabin282k, sweep256, cabin2m, adjoint64, resonance64."""
     if name == "box100":
         return Workload(name, [small_box_problem()], np.array([100.0]), "gmres", restart=30)
     if name == "cabin282k":
@@ -228,6 +245,9 @@ def workload(name: str) -> Workload:
                         "cocg", mixed=True)
     if name == "adjoint64":
         return Workload(name, [cabin_problem(100, 56, 48)], np.geomspace(20.0, 300.0, 64), "cocg")
+    if name == "resonance64":
+        # the sun-roof pattern of cabin_problem scaled per frequency by resonance_spectrum(f)
+        return Workload(name, [cabin_problem(100, 56, 48)], resonance_freqs(64), "cocg")
     raise KeyError(name)
 
 

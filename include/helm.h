@@ -62,39 +62,56 @@ typedef enum {
 
 enum { HELM_C128 = 0, HELM_C64 = 1 };                 /* matrix value precision */
 enum { HELM_FMT_CSR = 0, HELM_FMT_DIA27 = 1 };         /* matrix layout (see helm_assemble) */
-enum { HELM_SOLVER_GMRES = 0, HELM_SOLVER_COCG = 1 }; /* Krylov method */
-enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1 }; /* right preconditioner (GMRES only) */
+enum { HELM_SOLVER_GMRES = 0, HELM_SOLVER_COCG = 1, HELM_SOLVER_BICGSTAB = 2, HELM_SOLVER_TFQMR = 3 }; /* Krylov method */
+enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1, HELM_PRECOND_JACOBI = 2 }; /* right preconditioner */
 
 typedef struct {
   int32_t solver;       /* HELM_SOLVER_GMRES: restarted GMRES(restart), CGS2 Arnoldi, complex
-                           Givens; HELM_SOLVER_COCG: conjugate-orthogonal CG (A complex symmetric) */
+                           Givens; HELM_SOLVER_COCG: conjugate-orthogonal CG (A complex symmetric);
+                           HELM_SOLVER_BICGSTAB: BiCGSTAB (paper Sec. 4, Table 3),
+                           stats.iterations counts iterations of two SpMVs;
+                           HELM_SOLVER_TFQMR: transpose-free QMR (paper Sec. 4, Table 3),
+                           stats.iterations counts steps (one SpMV each on average) */
   int32_t restart;      /* GMRES cycle length m (1..128) */
   double tol;           /* stop when the true ||b - A p||_2 / ||b||_2 <= tol */
   int32_t maxit;        /* Krylov steps (SpMVs inside the iteration) before HELM_NOT_CONVERGED */
-  int32_t precond;      /* HELM_PRECOND_NONE or HELM_PRECOND_RAS (GMRES only) */
+  int32_t precond;      /* HELM_PRECOND_NONE; HELM_PRECOND_RAS (GMRES only); HELM_PRECOND_JACOBI
+                           (not GMRES), the reading of the paper's unnamed "P": BiCGSTAB / TFQMR
+                           run on A D^-1 (D = diag(A), right Jacobi) and return x = D^-1 y; COCG
+                           (FP64 or mixed) runs on S A S with S = D^-1/2 (principal root; stays
+                           complex symmetric), b scaled by S, residual norms weighted by |a_ii|,
+                           and returns x = S y. Either way tol and stats.relres refer to
+                           A x = b */
   int32_t ras_parts[3]; /* Schwarz blocks along x, y, z */
   int32_t ras_overlap;  /* lattice layers of overlap */
-  int32_t mixed;        /* 1: FP64 iterative refinement around a complex64 inner COCG (COCG only);
-                           a system whose refinement step fails to halve the FP64 residual is
-                           restarted as FP64 COCG from zero (stats.outer < 0 marks such a
-                           fallback: -outer refinement steps were taken before it) */
-  double inner_tol;     /* mixed: inner relative residual reduction per refinement step */
+  int32_t mixed;        /* 0: FP64 COCG. 1: FP64 iterative refinement around a complex64 inner
+                           COCG. 2: the same around a double-word inner COCG (every inner value a
+                           pair of floats hi + lo, about 48 significand bits, computed on the
+                           FP32 pipe; no counterpart in the paper, a GB300 choice: its FP64 rate
+                           is 1/64 of its FP32 rate). COCG only. A system whose refinement step
+                           fails to halve the FP64 residual is restarted as FP64 COCG from zero
+                           (stats.outer < 0 marks such a fallback: -outer refinement steps were
+                           taken before it) */
+  double inner_tol;     /* mixed: inner relative residual reduction per refinement step; an inner
+                           solve also stops once its residual reaches tol * ||b|| / 2, and (with
+                           stall_window) when its estimate stops halving */
   int32_t inner_maxit;  /* mixed: inner steps per refinement step */
   int32_t max_outer;    /* mixed: refinement steps before HELM_NOT_CONVERGED */
   int32_t stall_window; /* COCG: if the residual estimate has not halved its best value within
                            this many steps, check the true residual and restart from the current
-                           iterate (0 = never; counted in stats.restarts) */
+                           iterate (0 = never; counted in stats.restarts); mixed: end the inner
+                           solve (the next refinement step restarts from the current iterate) */
   int32_t pad_;
 } helm_solve_opts;
 
 typedef struct {
   int32_t status;       /* helm_status of this system */
-  int32_t iterations;   /* Krylov steps (inner complex64 steps when mixed) */
+  int32_t iterations;   /* Krylov steps (inner steps included when mixed) */
   int32_t restarts;     /* GMRES cycles - 1 / COCG residual-replacement restarts */
   int32_t outer;        /* mixed: refinement steps taken */
   double relres;        /* true FP64 ||b - A p|| / ||b|| at exit */
   double bnorm;         /* ||b||_2 */
-  int32_t iterations_c64; /* mixed: the complex64 inner steps among `iterations` */
+  int32_t iterations_c64; /* mixed: the inner (complex64 or double-word) steps among `iterations` */
   int32_t pad;
 } helm_solve_stats;
 
@@ -137,9 +154,11 @@ helm_status helm_sizes(const helm_ctx* ctx, int64_t* n_nodes, int64_t* nnz, int6
  * in `precision` (HELM_C128, or HELM_C64: complex64 values rounded from the complex128 ones)
  * and `format`:
  *   HELM_FMT_CSR   -- compressed sparse rows (paper Sec. 4), the context's 27-point pattern;
- *   HELM_FMT_DIA27 -- slot-major 27-point layout: val[k * n + row], k = (di+1) + 3 (dj+1) +
- *                     9 (dl+1) for the neighbour row + di + (nx+1) (dj + (ny+1) dl); slots whose
- *                     neighbour is outside the lattice hold zero. Same values as the CSR form.
+ *   HELM_FMT_DIA27 -- slot-major 27-point layout with real and imaginary parts split: 27 n real
+ *                     parts re[k * n + row] followed by 27 n imaginary parts im[k * n + row]
+ *                     (FP64, or FP32 for HELM_C64), k = (di+1) + 3 (dj+1) + 9 (dl+1) for the
+ *                     neighbour row + di + (nx+1) (dj + (ny+1) dl); slots whose neighbour is
+ *                     outside the lattice hold zero. Same values as the CSR form.
  * If b_out (dev, complex128 [n]) is not NULL the lifted right-hand side b_F = -A_FD p_D,
  * b_D = p_D is written there. *A_out is owned by the caller's handle until helm_matrix_free and
  * must be freed before its context. */
@@ -153,7 +172,8 @@ void helm_matrix_free(helm_matrix* A);
 helm_status helm_matrix_csr(const helm_matrix* A, int64_t* n, int64_t* nnz, int32_t* precision,
                             const int32_t** rowptr, const int32_t** col, const void** val);
 
-/* Read-only view of a DIA27 matrix: val (dev complex [27 n], layout above). HELM_ERR_ARG for CSR. */
+/* Read-only view of a DIA27 matrix: val (dev, 54 n reals: 27 n real parts then 27 n imaginary
+ * parts, layout above). HELM_ERR_ARG for CSR. */
 helm_status helm_matrix_dia27(const helm_matrix* A, int64_t* n, int32_t* precision, const void** val);
 
 /* y = A x (paper Sec. 4: "the most time consuming operation") for either layout. x, y (dev)
@@ -186,8 +206,8 @@ helm_status helm_reduce_noalloc(int32_t op, int64_t n, const double* x, const do
 
 /* Frequency response: solve the system of every frequency freqs_hz[0..nfreq) (host) on the
  * context's lattice. p_out (dev, complex128 [nfreq][n]) receives the pressure (the best
- * iterate if not converged); stats (host, [nfreq]) the per-frequency statistics. COCG systems
- * (FP64 or mixed) advance together in one persistent cooperative launch; GMRES systems run
+ * iterate if not converged); stats (host, [nfreq]) the per-frequency statistics. COCG,
+ * BiCGSTAB and TFQMR systems (COCG: FP64 or mixed) advance together in one persistent cooperative launch; GMRES systems run
  * one after another, each restart cycle a captured CUDA graph. Synchronises the stream.
  * Returns HELM_OK if every system converged, else the first failing status. */
 helm_status helm_solve(helm_ctx* ctx, const double* freqs_hz, int32_t nfreq,
@@ -195,7 +215,7 @@ helm_status helm_solve(helm_ctx* ctx, const double* freqs_hz, int32_t nfreq,
 
 /* Batched frequency-response sweep over systems that may live on different lattices:
  * system s is context ctxs[s] (host array) at frequency freqs_hz[s] (host); its pressure goes
- * to p_out[s] (host array of dev pointers, complex128 [n_s]). COCG only (FP64 or mixed); all
+ * to p_out[s] (host array of dev pointers, complex128 [n_s]). COCG (FP64 or mixed), BiCGSTAB or TFQMR; all
  * systems advance together in one persistent cooperative launch. Synchronises the first
  * context's stream. */
 helm_status helm_solve_batch(helm_ctx* const* ctxs, const double* freqs_hz, int32_t nsys,

@@ -48,14 +48,19 @@ __global__ void scatter_dirichlet(const int32_t* __restrict__ nodes, const cd* _
 
 bool valid_opts(const helm_solve_opts* o) {
   if (!o) return false;
-  if (o->solver != HELM_SOLVER_GMRES && o->solver != HELM_SOLVER_COCG) return false;
+  if (o->solver != HELM_SOLVER_GMRES && o->solver != HELM_SOLVER_COCG && o->solver != HELM_SOLVER_BICGSTAB &&
+      o->solver != HELM_SOLVER_TFQMR)
+    return false;
   if (!(o->tol > 0.0) || o->maxit < 1) return false;
   if (o->solver == HELM_SOLVER_GMRES && (o->restart < 1 || o->restart > 128)) return false;
-  if (o->precond != HELM_PRECOND_NONE && o->precond != HELM_PRECOND_RAS) return false;
+  if (o->precond != HELM_PRECOND_NONE && o->precond != HELM_PRECOND_RAS && o->precond != HELM_PRECOND_JACOBI)
+    return false;
+  if (o->precond == HELM_PRECOND_JACOBI && o->solver == HELM_SOLVER_GMRES) return false;
   if (o->precond == HELM_PRECOND_RAS) {
     if (o->solver != HELM_SOLVER_GMRES) return false;
     if (o->ras_parts[0] < 1 || o->ras_parts[1] < 1 || o->ras_parts[2] < 1 || o->ras_overlap < 0) return false;
   }
+  if (o->mixed < 0 || o->mixed > 2) return false;
   if (o->mixed) {
     if (o->solver != HELM_SOLVER_COCG) return false;
     if (!(o->inner_tol > 0.0) || o->inner_maxit < 1 || o->max_outer < 1) return false;
@@ -294,7 +299,7 @@ helm_status helm_solve(helm_ctx* c, const double* freqs_hz, int32_t nfreq, const
     if (!(freqs_hz[f] >= 0) || !std::isfinite(freqs_hz[f])) return set_error(HELM_ERR_ARG, "helm_solve: bad frequency");
   if (nfreq == 0) return HELM_OK;
   memset(&last_profile(), 0, sizeof(helm_profile));
-  if (opts->solver == HELM_SOLVER_COCG) {
+  if (opts->solver == HELM_SOLVER_COCG || opts->solver == HELM_SOLVER_BICGSTAB || opts->solver == HELM_SOLVER_TFQMR) {
     std::vector<BatchSystem> sys(nfreq);
     for (int f = 0; f < nfreq; ++f) sys[f] = BatchSystem{c, freqs_hz[f], (cd*)p_out + (size_t)f * c->n, &stats[f], nullptr};
     return solve_cocg_batch(sys.data(), nfreq, *opts, c->stream);
@@ -312,8 +317,8 @@ helm_status helm_solve(helm_ctx* c, const double* freqs_hz, int32_t nfreq, const
 helm_status helm_solve_batch(helm_ctx* const* ctxs, const double* freqs_hz, int32_t nsys, const helm_solve_opts* opts,
                              double* const* p_out, helm_solve_stats* stats) {
   if (!ctxs || !freqs_hz || !p_out || !stats || nsys < 0) return set_error(HELM_ERR_ARG, "helm_solve_batch: bad argument");
-  if (!valid_opts(opts) || opts->solver != HELM_SOLVER_COCG)
-    return set_error(HELM_ERR_ARG, "helm_solve_batch: invalid options (COCG only)");
+  if (!valid_opts(opts) || opts->solver == HELM_SOLVER_GMRES)
+    return set_error(HELM_ERR_ARG, "helm_solve_batch: invalid options (COCG, BiCGSTAB or TFQMR)");
   if (nsys == 0) return HELM_OK;
   memset(&last_profile(), 0, sizeof(helm_profile));
   std::vector<BatchSystem> sys(nsys);

@@ -88,8 +88,9 @@ __device__ inline void side_term(const cd* __restrict__ beta, int64_t base, int 
     }
 }
 
-// DIA = false: CSR values at rowptr[r]..; DIA = true: slot-major values val[k * n + r] with
-// k = (di+1) + 3 (dj+1) + 9 (dl+1) and zeros for neighbours outside the lattice.
+// DIA = false: CSR values at rowptr[r]..; DIA = true: slot-major split layout, real parts at
+// vre[k * n + r] and imaginary parts at vim[k * n + r] (vre = (double*)val, vim = vre + 27 n),
+// k = (di+1) + 3 (dj+1) + 9 (dl+1), zeros for neighbours outside the lattice.
 template <bool DIA>
 __global__ void values_kernel(Lattice L, double k2, double krc, const int32_t* __restrict__ rowptr,
                               const cd* __restrict__ beta, const uint8_t* __restrict__ is_dir,
@@ -107,8 +108,13 @@ __global__ void values_kernel(Lattice L, double k2, double krc, const int32_t* _
   cd bsum(0.0, 0.0);
   bool row_complex = false;
   int64_t k = DIA ? 0 : rowptr[r];
+  double* vre = reinterpret_cast<double*>(val);
+  double* vim = vre + 27 * n;
   if (DIA)
-    for (int s = 0; s < 27; ++s) val[(int64_t)s * n + r] = cd(0.0, 0.0);
+    for (int s = 0; s < 27; ++s) {
+      vre[(int64_t)s * n + r] = 0.0;
+      vim[(int64_t)s * n + r] = 0.0;
+    }
   for (int dl = -1; dl <= 1; ++dl) {
     if (l + dl < 0 || l + dl >= L.Nz) continue;
     double kz, mz;
@@ -145,9 +151,14 @@ __global__ void values_kernel(Lattice L, double k2, double krc, const int32_t* _
           bsum.im += a.re * pc.im + a.im * pc.re;
           a = cd(0.0, 0.0);
         }
-        val[k] = a;
+        if (DIA) {
+          vre[k] = a.re;
+          vim[k] = a.im;
+        } else {
+          val[k] = a;
+          ++k;
+        }
         row_complex |= (a.im != 0.0);
-        if (!DIA) ++k;
       }
     }
   }
@@ -184,6 +195,25 @@ helm_status assemble_values(const helm_ctx* ctx, double freq, cd* val, cd* b, cu
   (dia ? values_kernel<true> : values_kernel<false>)<<<(unsigned)blocks, T, 0, s>>>(L, k * k, k * ctx->phys.rho * ctx->phys.c, ctx->rowptr,
                                                ctx->beta, eliminate ? ctx->is_dir : nullptr,
                                                ctx->p_dir_full, val, eliminate ? b : nullptr, cflag, ctx->n);
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
+}
+
+// Double-word copy of m doubles: out[t] = (hi, lo), hi = fl32(v), lo = fl32(v - hi).
+__global__ void split_kernel(const double* __restrict__ v, float2* __restrict__ out, int64_t m) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; t < m; t += stride) {
+    const double a = v[t];
+    const float hi = __double2float_rn(a);
+    out[t] = make_float2(hi, __double2float_rn(a - (double)hi));
+  }
+}
+
+helm_status split_values(const double* val, float2* out, int64_t m, cudaStream_t s) {
+  if (m == 0) return HELM_OK;
+  int blocks = (int)std::min<int64_t>((m + 255) / 256, 152 * 16);
+  split_kernel<<<blocks, 256, 0, s>>>(val, out, m);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }

@@ -115,6 +115,8 @@ helm_status build_pattern(helm_ctx* ctx);
 helm_status assemble_values(const helm_ctx* ctx, double freq, cd* val, cd* b, cudaStream_t s,
                             bool eliminate = true, bool dia = false, uint8_t* cflag = nullptr);
 helm_status cast_values(const cd* val, cf* val32, int64_t nnz, cudaStream_t s);
+// double-word (hi, lo) float pairs of m doubles
+helm_status split_values(const double* val, float2* out, int64_t m, cudaStream_t s);
 
 // spmv.cu
 helm_status spmv_c128(const int32_t* rowptr, const int32_t* col, const cd* val, const cd* x, cd* y,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dw.cuh"
 
 namespace helm {
 
@@ -111,22 +112,25 @@ __device__ __forceinline__ cplx<T> csr_row27(const int32_t* __restrict__ rowptr,
 }
 
 // ---------------------------------------------------------------------------------------------
-// Slot-major 27-point layout ("DIA-27"): val[k * n + row] holds the entry of `row` for lattice
-// offset k = (di+1) + 3 (dj+1) + 9 (dl+1), column row + di + Nx (dj + Ny dl); entries whose
-// neighbour lies outside the lattice are stored as zero. One thread per row: the value loads
+// Slot-major 27-point layout ("DIA-27"), real and imaginary parts in separate arrays:
+// vre[k * n + row] / vim[k * n + row] hold the entry of `row` for lattice offset
+// k = (di+1) + 3 (dj+1) + 9 (dl+1), column row + di + Nx (dj + Ny dl); entries whose neighbour
+// lies outside the lattice are stored as zero. The two arrays are contiguous: vim = vre + 27 n. One thread per row: the value loads
 // and the x gathers of a warp are contiguous, no column indices are read, and no lanes are
 // idle. Gather indices are clamped into [0, n) so that padded slots (value 0) read a valid
 // address; 0 * x adds nothing for finite x, so the clamp never changes a result. A per-row
 // byte flag (set at assembly) marks rows with a non-zero imaginary entry.
 // ---------------------------------------------------------------------------------------------
-// Real-part product of one row: sum_k Re(a_k) x_{c_k}. Three independent accumulation chains
-// per component (one per stencil line dj = -1, 0, 1), so consecutive multiply-adds do not wait
-// on each other. Complex entries occur only next to admittance walls; their imaginary parts are
-// added by dia_row_im in a second pass that only rows flagged at assembly take -- on GB300 the
-// FP64 pipe is the bottleneck, so the common real rows must not issue any imaginary FMA.
+// Real-part product of one row: sum_k Re(a_k) x_{c_k}, real parts stored slot-major in vre
+// (vre[k * n + row]). Three independent accumulation chains per component (one per stencil line
+// dj = -1, 0, 1), so consecutive multiply-adds do not wait on each other. Complex entries occur
+// only next to admittance walls; their imaginary parts (vim, same layout) are added by
+// dia_row_im in a second pass that only rows flagged at assembly take -- on GB300 the FP64 pipe
+// is the bottleneck, so the common real rows must not issue any imaginary FMA, and the real pass
+// streams 8 bytes per entry instead of 16.
 template <typename T>
-__device__ __forceinline__ cplx<T> dia_row_re(const cplx<T>* __restrict__ val, const cplx<T>* x, int64_t n,
-                                              int64_t Nx, int64_t NxNy, int64_t row) {
+__device__ __forceinline__ cplx<T> dia_row_re(const T* __restrict__ vre, const cplx<T>* x, int64_t n, int64_t Nx,
+                                              int64_t NxNy, int64_t row) {
   cplx<T> acc[3] = {cplx<T>(T(0), T(0)), cplx<T>(T(0), T(0)), cplx<T>(T(0), T(0))};
 #pragma unroll
   for (int dl = -1; dl <= 1; ++dl) {
@@ -138,7 +142,7 @@ __device__ __forceinline__ cplx<T> dia_row_re(const cplx<T>* __restrict__ val, c
       const int k = q + 9 * (dl + 1);
       int64_t c = row + di + Nx * dj + NxNy * dl;
       c = c < 0 ? 0 : (c >= n ? n - 1 : c);
-      a[q] = ld_stream(val + (int64_t)k * n + row).re;
+      a[q] = __ldcs(vre + (int64_t)k * n + row);
       xv[q] = x[c];
     }
 #pragma unroll
@@ -153,20 +157,75 @@ __device__ __forceinline__ cplx<T> dia_row_re(const cplx<T>* __restrict__ val, c
 
 // Imaginary-part product of one row: sum_k i Im(a_k) x_{c_k}.
 template <typename T>
-__device__ __forceinline__ cplx<T> dia_row_im(const cplx<T>* __restrict__ val, const cplx<T>* x, int64_t n,
-                                              int64_t Nx, int64_t NxNy, int64_t row) {
+__device__ __forceinline__ cplx<T> dia_row_im(const T* __restrict__ vim, const cplx<T>* x, int64_t n, int64_t Nx,
+                                              int64_t NxNy, int64_t row) {
   cplx<T> acc(T(0), T(0));
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
     const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dl = k / 9 - 1;
     int64_t c = row + di + Nx * dj + NxNy * dl;
     c = c < 0 ? 0 : (c >= n ? n - 1 : c);
-    const T b = val[(int64_t)k * n + row].im;
+    const T b = vim[(int64_t)k * n + row];
     const cplx<T> xv = x[c];
     acc.re = fma(-b, xv.im, acc.re);
     acc.im = fma(b, xv.re, acc.im);
   }
   return acc;
+}
+
+// Double-word versions of the two passes (matrix parts as (hi, lo) float pairs in the same
+// slot-major split layout, vectors as complex double-word): the products and sums run on the
+// FP32 pipe with Dot2-style error accumulation, three accumulators per component as above.
+__device__ __forceinline__ cw dia_row_re_dw(const float2* __restrict__ vre, const cw* x, int64_t n, int64_t Nx,
+                                            int64_t NxNy, int64_t row) {
+  dacc ar[3], ai[3];
+#pragma unroll
+  for (int dl = -1; dl <= 1; ++dl) {
+    float2 a[9];
+    cw xv[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const int di = q % 3 - 1, dj = q / 3 - 1;
+      const int k = q + 9 * (dl + 1);
+      int64_t c = row + di + Nx * dj + NxNy * dl;
+      c = c < 0 ? 0 : (c >= n ? n - 1 : c);
+      a[q] = __ldcs(vre + (int64_t)k * n + row);
+      xv[q] = x[c];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      ar[q / 3].mac(a[q].x, a[q].y, xv[q].rh, xv[q].rl);
+      ai[q / 3].mac(a[q].x, a[q].y, xv[q].ih, xv[q].il);
+    }
+  }
+  ar[0].add(ar[1]);
+  ar[0].add(ar[2]);
+  ai[0].add(ai[1]);
+  ai[0].add(ai[2]);
+  cw out;
+  ar[0].get(out.rh, out.rl);
+  ai[0].get(out.ih, out.il);
+  return out;
+}
+
+// i Im(a) x part of a flagged row: re -= Im(a) x.im, im += Im(a) x.re
+__device__ __forceinline__ cw dia_row_im_dw(const float2* __restrict__ vim, const cw* x, int64_t n, int64_t Nx,
+                                            int64_t NxNy, int64_t row) {
+  dacc ar, ai;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dl = k / 9 - 1;
+    int64_t c = row + di + Nx * dj + NxNy * dl;
+    c = c < 0 ? 0 : (c >= n ? n - 1 : c);
+    const float2 b = vim[(int64_t)k * n + row];
+    const cw xv = x[c];
+    ar.mac(-b.x, -b.y, xv.ih, xv.il);
+    ai.mac(b.x, b.y, xv.rh, xv.rl);
+  }
+  cw out;
+  ar.get(out.rh, out.rl);
+  ai.get(out.ih, out.il);
+  return out;
 }
 
 // Deterministic block sum of NV doubles per thread (fixed shuffle tree, then warps in order).

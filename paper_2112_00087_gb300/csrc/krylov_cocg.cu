@@ -29,210 +29,16 @@
 // effect only in phase C, so the loop-control values every block reads at the top of a step
 // are stable. Converged systems drop out of a compacted tile list.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
 
-#include "kernels.cuh"
+#include "krylov_engine.cuh"
 
 namespace helm {
 namespace {
-
-struct KSys {
-  int64_t n;
-  int64_t Nx, NxNy;   // lattice strides of the slot-major 27-point layout
-  const cd* val;      // [27][n] complex128
-  const cf* val32;    // [27][n] complex64 (mixed)
-  const uint8_t* cflag;  // [n] 1 for rows with a non-zero imaginary entry
-  const cd* b;
-  cd* x;
-  cd* r;
-  cd* p;
-  cd* q;
-  cf* x32;
-  cf* r32;
-  cf* p32;
-  cf* q32;
-  int tile0, ntiles;
-};
-
-enum : int { MODE_RESID = 0, MODE_INNER = 1, MODE_FP64 = 2 };
-enum : int { C_PUPDATE = 0, C_CHECK = 1, C_XUPDATE = 2 };
-
-struct KState {
-  int act;       // 1 while iterating
-  int amode;     // phase A source: 0 = p, 1 = r (and p := r)
-  int cmode;     // phase C action
-  int mode;      // mixed: MODE_RESID / MODE_INNER
-  int it;        // Krylov steps (complex64 inner and FP64 steps)
-  int it32;      // complex64 inner steps
-  int inner_it;
-  int outer;
-  int restarts;
-  int status;
-  int bd;        // breakdown seen
-  int pend;      // mixed: finish pending (status in `status`)
-  int to_fp64;   // mixed: switch to FP64 COCG at the end of this step
-  int discard;   // mixed: the inner solve did not reduce its residual; skip its correction
-  int fell_back; // mixed: the system finished in FP64 COCG
-  int reset_x;   // mixed: the fallback restarts from x = 0 (refinement left x worse than zero)
-  int best_it;   // step of the last halving of the best residual estimate
-  unsigned arrive;
-  double bnorm, rnorm, relres, est, prev_rel, best_est;
-  cd rho, alpha, beta;
-};
-
-struct KTile {
-  int sys;
-  int pad;
-  int64_t row0, row1;
-};
-
-enum : int { CTRL_CUR = 0, CTRL_CNT0 = 1, CTRL_CNT1 = 2, CTRL_NACT = 3, CTRL_FIN = 4, CTRL_N = 8 };
-
-struct KParams {
-  const KSys* sys;
-  KState* st;
-  const KTile* tiles;
-  int ntiles;
-  int* list0;
-  int* list1;
-  int* ctrl;
-  cd* part;  // [ntiles][2]
-  GridBar* bar;
-  double tol;
-  int maxit;
-  double inner_tol;
-  int inner_maxit;
-  int max_outer;
-  int max_steps;
-  int stall;
-  unsigned bar_extra;             // fault injection: arrivals the barriers wait for in addition
-  unsigned long long bar_timeout;  // barrier give-up time (ns)
-};
-
-
-__device__ __forceinline__ int vload(const int* p) { return *((volatile const int*)p); }
-
-// Arrival of this block's tile for system s; true (block-uniform) for the last arriver.
-__device__ __forceinline__ bool arrive_last(KState* S, int ntiles_s) {
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned old = atomicAdd(&S->arrive, 1u);
-    s_last = (old + 1u == (unsigned)ntiles_s);
-    if (s_last) {
-      S->arrive = 0u;
-      __threadfence();
-    }
-  }
-  __syncthreads();
-  return s_last != 0;
-}
-
-// Sum of the two complex partials of tiles [tile0, tile0 + nt), tile order, every thread.
-__device__ __forceinline__ void sum_parts(const cd* part, int tile0, int nt, cd& a, cd& b, double* sh) {
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int t = threadIdx.x; t < nt; t += kBlock) {
-    const cd u = ld_l2(part + 2 * (int64_t)(tile0 + t));
-    const cd w = ld_l2(part + 2 * (int64_t)(tile0 + t) + 1);
-    v[0] += u.re; v[1] += u.im; v[2] += w.re; v[3] += w.im;
-  }
-  block_sum<4>(v, sh);
-  a = cd(v[0], v[1]);
-  b = cd(v[2], v[3]);
-}
-
-__device__ __forceinline__ void write_parts(cd* part, int t, const double (&v)[4]) {
-  if (threadIdx.x == 0) {
-    part[2 * (int64_t)t] = cd(v[0], v[1]);
-    part[2 * (int64_t)t + 1] = cd(v[2], v[3]);
-  }
-}
-
-__device__ __forceinline__ void finish(const KParams& P, KState* S, int status, double relres) {
-  S->status = status;
-  S->relres = relres;
-  S->act = 0;
-  __threadfence();
-  atomicAdd(&P.ctrl[CTRL_FIN], 1);
-  atomicSub(&P.ctrl[CTRL_NACT], 1);
-}
-
-// Block 0, phase A: rebuild the other tile list from the act flags (only when a system
-// finished since the last rebuild). Act flags change only in phase C, so the snapshot is
-// exact. The list index is flipped by the caller in phase B, after every block has read the
-// current index for this step; the new list is consumed from the next step on.
-__device__ bool rebuild_list(const KParams& P, int cur, int& seen_fin, int* sh_int) {
-  const int fin = vload(&P.ctrl[CTRL_FIN]);
-  if (fin == seen_fin) return false;  // block-uniform: every thread read the same stable value
-  seen_fin = fin;
-  int* dst = cur ? P.list0 : P.list1;
-  int base = 0;
-  for (int t0 = 0; t0 < P.ntiles; t0 += kBlock) {
-    const int t = t0 + threadIdx.x;
-    const int keep = (t < P.ntiles) ? vload(&P.st[P.tiles[t].sys].act) : 0;
-    // block exclusive scan of keep (warp ballots, then warp counts in order)
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sh_int[w] = __popc(m);
-    __syncthreads();
-    int off = base;
-    for (int i = 0; i < w; ++i) off += sh_int[i];
-    int tot = 0;
-    for (int i = 0; i < kBlock / 32; ++i) tot += sh_int[i];
-    if (keep) dst[off + __popc(m & ((1u << lane) - 1u))] = t;
-    base += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    P.ctrl[cur ? CTRL_CNT0 : CTRL_CNT1] = base;
-    __threadfence();
-  }
-  return true;
-}
-
-// Product of the tile's rows with x in two passes: first(row, s_re, complex_flag) for every
-// row with the real-part product (two rows per thread, so their loads overlap), then, if any
-// row of the tile is flagged complex (block-uniform), fix(row, s_im) for each flagged row with
-// its imaginary-part product. Thread t handles rows row0 + t + m kBlock in both passes, so a
-// thread reads back only what it wrote itself.
-#ifndef HELM_ROWS_PER_THREAD
-#define HELM_ROWS_PER_THREAD 2
-#endif
-#ifndef HELM_VEC_UNROLL
-#define HELM_VEC_UNROLL 4
-#endif
-
-template <typename T, typename F1, typename F2>
-__device__ __forceinline__ void tile_spmv(const cplx<T>* val, const uint8_t* cflag, const cplx<T>* x, int64_t n,
-                                          int64_t Nx, int64_t NxNy, int64_t row0, int64_t row1, F1 first,
-                                          F2 fix) {
-  int has_c = 0;
-  if (HELM_ROWS_PER_THREAD == 2) {
-    for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += 2 * kBlock) {
-      const int64_t r1 = r0 + kBlock < row1 ? r0 + kBlock : r0;  // clamped only in a ragged tail
-      const cplx<T> s0 = dia_row_re<T>(val, x, n, Nx, NxNy, r0);
-      const cplx<T> s1 = dia_row_re<T>(val, x, n, Nx, NxNy, r1);
-      const int c0 = cflag[r0], c1 = cflag[r1];
-      first(r0, s0, c0);
-      if (r1 != r0) first(r1, s1, c1);
-      has_c |= c0 | c1;
-    }
-  } else {
-    for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += kBlock) {
-      const cplx<T> s0 = dia_row_re<T>(val, x, n, Nx, NxNy, r0);
-      const int c0 = cflag[r0];
-      first(r0, s0, c0);
-      has_c |= c0;
-    }
-  }
-  if (__syncthreads_or(has_c)) {
-    for (int64_t row = row0 + threadIdx.x; row < row1; row += kBlock)
-      if (cflag[row]) fix(row, dia_row_im<T>(val, x, n, Nx, NxNy, row));
-  }
-}
+using namespace eng;
 
 // ------------------------------- FP64 COCG phases ---------------------------------------------
 
@@ -247,7 +53,7 @@ __device__ void init_tile(const KParams& P, int t, double* sh, bool mixed) {
     Y.r[i] = bi;
     v[0] += bi.re * bi.re - bi.im * bi.im;
     v[1] += 2.0 * bi.re * bi.im;
-    v[2] += bi.re * bi.re + bi.im * bi.im;
+    v[2] += wnorm(Y, i) * (bi.re * bi.re + bi.im * bi.im);
   }
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
@@ -342,7 +148,7 @@ __device__ void phaseB_fp64(const KParams& P, int t, double* sh) {
         const cd ri = rv[u];
         v[0] += ri.re * ri.re - ri.im * ri.im;
         v[1] += 2.0 * ri.re * ri.im;
-        v[2] += ri.re * ri.re + ri.im * ri.im;
+        v[2] += wnorm(Y, i) * (ri.re * ri.re + ri.im * ri.im);
       }
     }
   }
@@ -401,10 +207,10 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
   }
   // true residual r = b - A x
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  auto add = [&](cd ri) {
+  auto add = [&](int64_t row, cd ri) {
     v[0] += ri.re * ri.re - ri.im * ri.im;
     v[1] += 2.0 * ri.re * ri.im;
-    v[2] += ri.re * ri.re + ri.im * ri.im;
+    v[2] += wnorm(Y, row) * (ri.re * ri.re + ri.im * ri.im);
   };
   tile_spmv<double>(
       Y.val, Y.cflag, Y.x, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
@@ -412,13 +218,13 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
         const cd bi = Y.b[row];
         const cd ri(bi.re - s.re, bi.im - s.im);
         Y.r[row] = ri;
-        if (!c) add(ri);
+        if (!c) add(row, ri);
       },
       [&](int64_t row, cd si) {
         const cd r0 = Y.r[row];
         const cd ri(r0.re - si.re, r0.im - si.im);
         Y.r[row] = ri;
-        add(ri);
+        add(row, ri);
       });
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
@@ -445,6 +251,59 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
 
 // ------------------------------- mixed-precision phases ---------------------------------------
 
+// FP64 true residual of a refinement step (both mixed variants), phase A.
+__device__ void resid_phaseA(const KParams& P, int t, double* sh, const KTile& T, KState* S, const KSys& Y) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  // FP64 true residual of the refinement (norm, and r^T r for a switch to FP64 COCG)
+  auto add = [&](int64_t row, cd ri) {
+    v[0] += ri.re * ri.re - ri.im * ri.im;
+    v[1] += 2.0 * ri.re * ri.im;
+    v[2] += wnorm(Y, row) * (ri.re * ri.re + ri.im * ri.im);
+  };
+  tile_spmv<double>(
+      Y.val, Y.cflag, Y.x, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
+      [&](int64_t row, cd s, int c) {
+        const cd bi = Y.b[row];
+        const cd ri(bi.re - s.re, bi.im - s.im);
+        Y.r[row] = ri;
+        if (!c) add(row, ri);
+      },
+      [&](int64_t row, cd si) {
+        const cd r0 = Y.r[row];
+        const cd ri(r0.re - si.re, r0.im - si.im);
+        Y.r[row] = ri;
+        add(row, ri);
+      });
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd rho, rr;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho, rr, sh);
+    if (threadIdx.x == 0) {
+      const double rel = sqrt(rr.re) / S->bnorm;
+      S->relres = rel;
+      S->pend = 0;
+      S->to_fp64 = 0;
+      if (rel <= P.tol) { S->pend = 1; S->status = HELM_OK; }
+      else if (!(rel == rel)) { S->pend = 1; S->status = HELM_NAN; }
+      else if (S->outer >= P.max_outer || S->it >= P.maxit) { S->pend = 1; S->status = HELM_NOT_CONVERGED; }
+      else if (S->outer >= 1 && rel > 0.5 * S->prev_rel) {
+        // complex64 refinement stalls on this system: restart it as FP64 COCG from x = 0
+        // (phase B sets x = 0, r = b). COCG's path on these indefinite systems depends on its
+        // starting vector; from zero the fallback runs exactly the plain FP64 iteration.
+        S->to_fp64 = 1;
+        S->reset_x = 1;
+        S->best_est = 1.0;
+        S->best_it = S->it;
+        S->rho = rho;
+        S->amode = 1;
+        S->bd = 0;
+      } else { S->rnorm = sqrt(rr.re); S->outer += 1; }
+      S->prev_rel = rel;
+    }
+  }
+}
+
 __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
   const KTile T = P.tiles[t];
   KState* S = P.st + T.sys;
@@ -452,54 +311,7 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
   const KSys Y = P.sys[T.sys];
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (vload(&S->mode) == MODE_RESID) {
-    // FP64 true residual of the refinement (norm, and r^T r for a switch to FP64 COCG)
-    auto add = [&](cd ri) {
-      v[0] += ri.re * ri.re - ri.im * ri.im;
-      v[1] += 2.0 * ri.re * ri.im;
-      v[2] += ri.re * ri.re + ri.im * ri.im;
-    };
-    tile_spmv<double>(
-        Y.val, Y.cflag, Y.x, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
-        [&](int64_t row, cd s, int c) {
-          const cd bi = Y.b[row];
-          const cd ri(bi.re - s.re, bi.im - s.im);
-          Y.r[row] = ri;
-          if (!c) add(ri);
-        },
-        [&](int64_t row, cd si) {
-          const cd r0 = Y.r[row];
-          const cd ri(r0.re - si.re, r0.im - si.im);
-          Y.r[row] = ri;
-          add(ri);
-        });
-    block_sum<4>(v, sh);
-    write_parts(P.part, t, v);
-    if (arrive_last(S, Y.ntiles)) {
-      cd rho, rr;
-      sum_parts(P.part, Y.tile0, Y.ntiles, rho, rr, sh);
-      if (threadIdx.x == 0) {
-        const double rel = sqrt(rr.re) / S->bnorm;
-        S->relres = rel;
-        S->pend = 0;
-        S->to_fp64 = 0;
-        if (rel <= P.tol) { S->pend = 1; S->status = HELM_OK; }
-        else if (!(rel == rel)) { S->pend = 1; S->status = HELM_NAN; }
-        else if (S->outer >= P.max_outer || S->it >= P.maxit) { S->pend = 1; S->status = HELM_NOT_CONVERGED; }
-        else if (S->outer >= 1 && rel > 0.5 * S->prev_rel) {
-          // complex64 refinement stalls on this system: restart it as FP64 COCG from x = 0
-          // (phase B sets x = 0, r = b). COCG's path on these indefinite systems depends on its
-          // starting vector; from zero the fallback runs exactly the plain FP64 iteration.
-          S->to_fp64 = 1;
-          S->reset_x = 1;
-          S->best_est = 1.0;
-          S->best_it = S->it;
-          S->rho = rho;
-          S->amode = 1;
-          S->bd = 0;
-        } else { S->rnorm = sqrt(rr.re); S->outer += 1; }
-        S->prev_rel = rel;
-      }
-    }
+    resid_phaseA(P, t, sh, T, S, Y);
     return;
   }
   // inner complex64 step: q32 = A32 src
@@ -544,6 +356,27 @@ __device__ void phaseA_mixed(const KParams& P, int t, double* sh) {
   }
 }
 
+// Fallback of a mixed system to FP64 COCG from x = 0: r = b, rho = b^T b (phase B).
+__device__ void fallback_phaseB(const KParams& P, int t, double* sh, const KTile& T, KState* S, const KSys& Y) {
+  if (!vload(&S->reset_x)) return;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  // restart from x = 0: r = b, rho = b^T b
+  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+    const cd bi = Y.b[i];
+    Y.x[i] = cd(0.0, 0.0);
+    Y.r[i] = bi;
+    v[0] += bi.re * bi.re - bi.im * bi.im;
+    v[1] += 2.0 * bi.re * bi.im;
+  }
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd rho, unused;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho, unused, sh);
+    if (threadIdx.x == 0) S->rho = rho;
+  }
+}
+
 __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
   const KTile T = P.tiles[t];
   KState* S = P.st + T.sys;
@@ -553,22 +386,7 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
   if (vload(&S->mode) == MODE_RESID) {
     if (vload(&S->pend)) return;
     if (vload(&S->to_fp64)) {
-      if (!vload(&S->reset_x)) return;
-      // restart from x = 0: r = b, rho = b^T b
-      for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-        const cd bi = Y.b[i];
-        Y.x[i] = cd(0.0, 0.0);
-        Y.r[i] = bi;
-        v[0] += bi.re * bi.re - bi.im * bi.im;
-        v[1] += 2.0 * bi.re * bi.im;
-      }
-      block_sum<4>(v, sh);
-      write_parts(P.part, t, v);
-      if (arrive_last(S, Y.ntiles)) {
-        cd rho, unused;
-        sum_parts(P.part, Y.tile0, Y.ntiles, rho, unused, sh);
-        if (threadIdx.x == 0) S->rho = rho;
-      }
+      fallback_phaseB(P, t, sh, T, S, Y);
       return;
     }
     // start an inner solve on r / ||r|| (complex64), x32 = 0
@@ -593,6 +411,8 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
         S->rho = rho;
         S->amode = 1;
         S->inner_it = 0;
+        S->best_est = 1.0;
+        S->best_it = 0;
         S->bd = 0;  // the mode itself changes in phase C (phase C of this step still reads it)
       }
     }
@@ -626,7 +446,7 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
         const cf ri = rv[u];
         acc[0] += ri.re * ri.re - ri.im * ri.im;
         acc[1] += 2.f * ri.re * ri.im;
-        acc[2] += ri.re * ri.re + ri.im * ri.im;
+        acc[2] += wnorm32(Y, i) * (ri.re * ri.re + ri.im * ri.im);
       }
     }
   }
@@ -642,7 +462,12 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
       const double est = sqrt(rr.re);  // relative to ||r / ||r|| || = 1
       S->est = est;
       S->amode = 0;
-      if (!(est > P.inner_tol) || S->inner_it >= P.inner_maxit || S->it >= P.maxit || S->bd) {
+      if (est < 0.5 * S->best_est) {
+        S->best_est = est;
+        S->best_it = S->inner_it;
+      }
+      if (!(est > inner_stop(P, S)) || S->inner_it >= P.inner_maxit || S->it >= P.maxit || S->bd ||
+          (P.stall > 0 && S->inner_it - S->best_it >= P.stall)) {
         S->cmode = C_XUPDATE;
         S->discard = !(est < 1.0);  // no reduction (or NaN): keep x, the residual test switches
       } else {
@@ -654,18 +479,24 @@ __device__ void phaseB_mixed(const KParams& P, int t, double* sh) {
   }
 }
 
+// End of a refinement residual step (both mixed variants), phase C: finish, fall back to FP64
+// COCG, or start the next inner solve.
+__device__ void resid_phaseC(const KParams& P, KState* S, const KSys& Y) {
+  const int pend = vload(&S->pend), to64 = vload(&S->to_fp64);
+  if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) {
+    if (pend) finish(P, S, S->status, S->relres);
+    else if (to64) { S->mode = MODE_FP64; S->fell_back = 1; }
+    else S->mode = MODE_INNER;
+  }
+}
+
 __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
   const KTile T = P.tiles[t];
   KState* S = P.st + T.sys;
   if (!vload(&S->act)) return;
   const KSys Y = P.sys[T.sys];
   if (vload(&S->mode) == MODE_RESID) {
-    const int pend = vload(&S->pend), to64 = vload(&S->to_fp64);
-    if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) {
-      if (pend) finish(P, S, S->status, S->relres);
-      else if (to64) { S->mode = MODE_FP64; S->fell_back = 1; }
-      else S->mode = MODE_INNER;
-    }
+    resid_phaseC(P, S, Y);
     return;
   }
   if (vload(&S->cmode) == C_PUPDATE) {
@@ -705,14 +536,177 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
   if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) S->mode = MODE_RESID;
 }
 
+// ------------------------------- double-word mixed phases -------------------------------------
+// Same refinement as above; the inner COCG runs in double-word arithmetic (dw.cuh): matrix,
+// vectors and every inner product and update carried as pairs of floats on the FP32 pipe, the
+// per-thread dot-product partials converted to FP64 once per phase. Refinement residuals,
+// the correction x += ||r|| d and all scalar decisions stay FP64.
+
+__device__ void phaseA_dw(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  if (vload(&S->mode) == MODE_RESID) {
+    resid_phaseA(P, t, sh, T, S, Y);
+    return;
+  }
+  const int amode = vload(&S->amode);
+  const cw* src = amode ? Y.rw : Y.pw;
+  dacc dr, di;  // p^T q
+  tile_spmv_dw(
+      Y.valw, Y.cflag, src, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
+      [&](int64_t row, cw q, int c) {
+        Y.qw[row] = q;
+        const cw pi = src[row];
+        if (amode) Y.pw[row] = pi;
+        if (!c) cw_dotu_acc(dr, di, pi, q);
+      },
+      [&](int64_t row, cw qi) {
+        const cw q = cw_add(Y.qw[row], qi);
+        Y.qw[row] = q;
+        cw_dotu_acc(dr, di, src[row], q);
+      });
+  double v[4] = {dr.to_double(), di.to_double(), 0.0, 0.0};
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd mu, unused;
+    sum_parts(P.part, Y.tile0, Y.ntiles, mu, unused, sh);
+    if (threadIdx.x == 0) {
+      S->it += 1;
+      S->it32 += 1;
+      S->inner_it += 1;
+      const cd rho = S->rho;
+      if ((mu.re == 0.0 && mu.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0)) {
+        S->bd = 1;
+        S->alpha = cd(0.0, 0.0);
+      } else {
+        S->alpha = cdiv(rho, mu);
+      }
+    }
+  }
+}
+
+__device__ void phaseB_dw(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  if (vload(&S->mode) == MODE_RESID) {
+    if (vload(&S->pend)) return;
+    if (vload(&S->to_fp64)) {
+      fallback_phaseB(P, t, sh, T, S, Y);
+      return;
+    }
+    // start an inner solve on r / ||r|| (double-word), d = 0
+    const double sc = 1.0 / S->rnorm;
+    dacc rr_, ri_;
+    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+      const cd ri = Y.r[i];
+      cw w;
+      split_double(ri.re * sc, w.rh, w.rl);
+      split_double(ri.im * sc, w.ih, w.il);
+      Y.rw[i] = w;
+      Y.xw[i] = cw{0.f, 0.f, 0.f, 0.f};
+      cw_dotu_acc(rr_, ri_, w, w);
+    }
+    double v[4] = {rr_.to_double(), ri_.to_double(), 0.0, 0.0};
+    block_sum<4>(v, sh);
+    write_parts(P.part, t, v);
+    if (arrive_last(S, Y.ntiles)) {
+      cd rho, unused;
+      sum_parts(P.part, Y.tile0, Y.ntiles, rho, unused, sh);
+      if (threadIdx.x == 0) {
+        S->rho = rho;
+        S->amode = 1;
+        S->inner_it = 0;
+        S->best_est = 1.0;
+        S->best_it = 0;
+        S->bd = 0;  // the mode itself changes in phase C
+      }
+    }
+    return;
+  }
+  const cd al = S->alpha;
+  const cws a = to_cws(al.re, al.im);
+  const cws ma = to_cws(-al.re, -al.im);
+  dacc rr_, ri_;
+  float nrm = 0.f;  // ||r||^2 for the stopping estimate (FP32 is enough for a threshold test)
+  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+    const cw pv = Y.pw[i], qv = Y.qw[i];
+    const cw xn = cw_axpy(Y.xw[i], a, pv);
+    const cw rn = cw_axpy(Y.rw[i], ma, qv);
+    Y.xw[i] = xn;
+    Y.rw[i] = rn;
+    cw_dotu_acc(rr_, ri_, rn, rn);
+    nrm = fmaf(wnorm32(Y, i), fmaf(rn.rh, rn.rh, rn.ih * rn.ih), nrm);
+  }
+  double v[4] = {rr_.to_double(), ri_.to_double(), (double)nrm, 0.0};
+  block_sum<4>(v, sh);
+  write_parts(P.part, t, v);
+  if (arrive_last(S, Y.ntiles)) {
+    cd rho_new, rr;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho_new, rr, sh);
+    if (threadIdx.x == 0) {
+      const double est = sqrt(rr.re);  // relative to ||r / ||r|| || = 1
+      S->est = est;
+      S->amode = 0;
+      if (est < 0.5 * S->best_est) {
+        S->best_est = est;
+        S->best_it = S->inner_it;
+      }
+      if (!(est > inner_stop(P, S)) || S->inner_it >= P.inner_maxit || S->it >= P.maxit || S->bd ||
+          (P.stall > 0 && S->inner_it - S->best_it >= P.stall)) {
+        S->cmode = C_XUPDATE;
+        S->discard = !(est < 1.0);
+      } else {
+        S->beta = cdiv(rho_new, S->rho);
+        S->rho = rho_new;
+        S->cmode = C_PUPDATE;
+      }
+    }
+  }
+}
+
+__device__ void phaseC_dw(const KParams& P, int t, double* sh) {
+  const KTile T = P.tiles[t];
+  KState* S = P.st + T.sys;
+  if (!vload(&S->act)) return;
+  const KSys Y = P.sys[T.sys];
+  if (vload(&S->mode) == MODE_RESID) {
+    resid_phaseC(P, S, Y);
+    return;
+  }
+  if (vload(&S->cmode) == C_PUPDATE) {
+    const cd be = S->beta;
+    const cws b = to_cws(be.re, be.im);
+    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) Y.pw[i] = cw_axpy(Y.rw[i], b, Y.pw[i]);
+    return;
+  }
+  // refinement update x += ||r|| d (FP64)
+  const double sc = vload(&S->discard) ? 0.0 : S->rnorm;
+  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
+    const cw d = Y.xw[i];
+    cd xi = Y.x[i];
+    xi.re = fma(sc, join_double(d.rh, d.rl), xi.re);
+    xi.im = fma(sc, join_double(d.ih, d.il), xi.im);
+    Y.x[i] = xi;
+  }
+  if (arrive_last(S, Y.ntiles) && threadIdx.x == 0) S->mode = MODE_RESID;
+}
+
 // A mixed-precision system that fell back to FP64 COCG (its mode changes only in phase C, after
 // every tile of the system has arrived, so all blocks see one mode per step).
 __device__ __forceinline__ bool in_fp64(const KParams& P, int t) {
   return vload(&P.st[P.tiles[t].sys].mode) == MODE_FP64;
 }
 
-template <bool MIXED, int MINB>
+// PREC: 0 = FP64 COCG, 1 = complex64 inner + FP64 refinement, 2 = double-word inner + FP64
+// refinement.
+template <int PREC, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
+  constexpr bool MIXED = PREC != 0;
   __shared__ double sh[4 * (kBlock / 32)];
   __shared__ int sh_int[kBlock / 32];
   const unsigned nb = gridDim.x;
@@ -727,21 +721,30 @@ __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
     bool rebuilt = false;
     if (blockIdx.x == 0) rebuilt = rebuild_list(P, cur, seen_fin, sh_int);
     for (int a = blockIdx.x; a < nat; a += nb) {
-      if (MIXED && !in_fp64(P, list[a])) phaseA_mixed(P, list[a], sh);
+      if (PREC == 1 && !in_fp64(P, list[a])) phaseA_mixed(P, list[a], sh);
+      else if (PREC == 2 && !in_fp64(P, list[a])) phaseA_dw(P, list[a], sh);
       else phaseA_fp64(P, list[a], sh);
     }
+    trace_mark(P, step, 0);
     if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
+    trace_mark(P, step, 1);
     if (rebuilt && threadIdx.x == 0) P.ctrl[CTRL_CUR] = cur ^ 1;
     for (int a = blockIdx.x; a < nat; a += nb) {
-      if (MIXED && !in_fp64(P, list[a])) phaseB_mixed(P, list[a], sh);
+      if (PREC == 1 && !in_fp64(P, list[a])) phaseB_mixed(P, list[a], sh);
+      else if (PREC == 2 && !in_fp64(P, list[a])) phaseB_dw(P, list[a], sh);
       else phaseB_fp64(P, list[a], sh);
     }
+    trace_mark(P, step, 2);
     if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
+    trace_mark(P, step, 3);
     for (int a = blockIdx.x; a < nat; a += nb) {
-      if (MIXED && !in_fp64(P, list[a])) phaseC_mixed(P, list[a], sh);
+      if (PREC == 1 && !in_fp64(P, list[a])) phaseC_mixed(P, list[a], sh);
+      else if (PREC == 2 && !in_fp64(P, list[a])) phaseC_dw(P, list[a], sh);
       else phaseC_fp64(P, list[a], sh);
     }
+    trace_mark(P, step, 4);
     if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
+    trace_mark(P, step, 5);
   }
 }
 
@@ -762,20 +765,30 @@ inline size_t rnd(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
 
 helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_opts& o, cudaStream_t s) {
   if (nsys <= 0) return HELM_OK;
-  const bool mixed = o.mixed != 0;
+  const int prec = o.mixed;  // 0 FP64, 1 complex64 inner, 2 double-word inner
+  const bool mixed = prec != 0;
   int dev = 0, nsm = 1;
   HELM_CUDA(cudaGetDevice(&dev));
   HELM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   int coop = 0;
   HELM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return set_error(HELM_ERR_CUDA, "device does not support cooperative launch");
-  // Two register budgets: one block per SM (255 registers, no spills, deep per-thread ILP) or
-  // two (128 registers). HELM_PERSIST_BLOCKS_PER_SM=2 selects the second (tuning knob).
+  // Register budgets: 1 block per SM (255 registers, deep per-thread ILP) up to 4 (64
+  // registers, more resident warps); HELM_PERSIST_BLOCKS_PER_SM selects one (tuning knob).
   const char* env = getenv("HELM_PERSIST_BLOCKS_PER_SM");
-  const int want = (env && atoi(env) == 2) ? 2 : 1;
+  const int want = env ? std::max(1, std::min(atoi(env), 4)) : HELM_DEFAULT_BLOCKS_PER_SM;
+  const bool bicg = o.solver == HELM_SOLVER_BICGSTAB;
+  const bool tfq = o.solver == HELM_SOLVER_TFQMR;
+  const bool jac = o.precond == HELM_PRECOND_JACOBI && (bicg || tfq);   // right Jacobi A D^-1
+  const bool sjac = o.precond == HELM_PRECOND_JACOBI && !(bicg || tfq);  // symmetric S A S (COCG)
   void (*kern)(KParams) = nullptr;
-  if (want == 2) kern = mixed ? cocg_persistent<true, 2> : cocg_persistent<false, 2>;
-  else kern = mixed ? cocg_persistent<true, 1> : cocg_persistent<false, 1>;
+  if (bicg) kern = reinterpret_cast<void (*)(KParams)>(bicg_kernel(want));
+  else if (tfq) kern = reinterpret_cast<void (*)(KParams)>(tfqmr_kernel(want));
+  else if (prec == 2) kern = want >= 2 ? cocg_persistent<2, 2> : cocg_persistent<2, 1>;
+  else if (want == 4) kern = mixed ? cocg_persistent<1, 4> : cocg_persistent<0, 4>;
+  else if (want == 3) kern = mixed ? cocg_persistent<1, 3> : cocg_persistent<0, 3>;
+  else if (want == 2) kern = mixed ? cocg_persistent<1, 2> : cocg_persistent<0, 2>;
+  else kern = mixed ? cocg_persistent<1, 1> : cocg_persistent<0, 1>;
   int per_sm = 0;
   HELM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return set_error(HELM_ERR_CUDA, "persistent kernel cannot be resident");
@@ -801,9 +814,17 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   for (int k = 0; k < nsys; ++k) {
     const size_t n = sys[k].ctx->n, nnz = 27 * n;  // slot-major 27-point values
     bytes += rnd(nnz * sizeof(cd)) + rnd(n * sizeof(cd)) * 2 + rnd(n);  // val, b, r, row flags
-    if (mixed) bytes += rnd(nnz * sizeof(cf)) + 4 * rnd(n * sizeof(cf));
+    if (prec == 1) bytes += rnd(nnz * sizeof(cf)) + 4 * rnd(n * sizeof(cf));
+    if (prec == 2) bytes += rnd(nnz * 2 * sizeof(float2)) + 4 * rnd(n * sizeof(cw));
     bytes += 2 * rnd(n * sizeof(cd));  // p, q (FP64 COCG, also the fallback of the mixed solver)
+    if (bicg || tfq) bytes += 3 * rnd(n * sizeof(cd));  // rs, s, t (TFQMR: r0*, w, A u)
+    if (tfq) bytes += rnd(n * sizeof(cd));              // TFQMR direction d
+    if (jac) bytes += rnd(n * sizeof(cd));              // diag(A)
+    if (sjac) bytes += rnd(n * sizeof(cd)) + rnd(n * sizeof(double)) + (mixed ? rnd(n * sizeof(float)) : 0);
   }
+  const char* tenv = getenv("HELM_TRACE_STEPS");
+  const int trace_steps = tenv ? std::max(0, std::min(atoi(tenv), 100000)) : 0;
+  bytes += rnd((size_t)trace_steps * 6 * sizeof(unsigned long long));
   bytes += rnd(nsys * sizeof(KSys)) + rnd(nsys * sizeof(KState)) + rnd(ntiles * sizeof(KTile)) +
            2 * rnd(ntiles * sizeof(int)) + rnd(CTRL_N * sizeof(int)) + rnd(2 * (size_t)ntiles * sizeof(cd)) +
            rnd(sizeof(GridBar));
@@ -832,7 +853,14 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     Y.b = b;
     Y.x = sys[k].p_out;
     Y.r = A.take<cd>(c->n);
-    if (mixed) {
+    if (prec == 2) {
+      Y.valw = A.take<float2>(54 * (size_t)c->n);
+      Y.xw = A.take<cw>(c->n);
+      Y.rw = A.take<cw>(c->n);
+      Y.pw = A.take<cw>(c->n);
+      Y.qw = A.take<cw>(c->n);
+    }
+    if (prec == 1) {
       cf* v32 = A.take<cf>(27 * (size_t)c->n);
       Y.val32 = v32;
       Y.x32 = A.take<cf>(c->n);
@@ -842,6 +870,22 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     }
     Y.p = A.take<cd>(c->n);
     Y.q = A.take<cd>(c->n);
+    if (bicg || tfq) {
+      Y.rs = A.take<cd>(c->n);
+      Y.sv = A.take<cd>(c->n);
+      Y.tv = A.take<cd>(c->n);
+    }
+    if (tfq) Y.dv = A.take<cd>(c->n);
+    if (jac) Y.djac = A.take<cd>(c->n);
+    double* wn = nullptr;
+    float* wn32 = nullptr;
+    if (sjac) {
+      Y.jsc = A.take<cd>(c->n);
+      wn = A.take<double>(c->n);
+      if (mixed) wn32 = A.take<float>(c->n);
+      Y.wn = wn;
+      Y.wn32 = wn32;
+    }
     Y.tile0 = tile0[k];
     Y.ntiles = ntl[k];
     st = assemble_values(c, sys[k].freq, val, b, s, true, /*dia=*/true, cflag);
@@ -849,7 +893,13 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
       cudaError_t ce = cudaMemcpyAsync(b, sys[k].rhs, c->n * sizeof(cd), cudaMemcpyDeviceToDevice, s);
       if (ce != cudaSuccess) st = cuda_error(ce, "rhs copy");
     }
-    if (st == HELM_OK && mixed) st = cast_values(val, const_cast<cf*>(Y.val32), 27 * c->n, s);
+    if (st == HELM_OK && sjac)
+      st = sym_jacobi_prepare(reinterpret_cast<double*>(val), cflag, b, Y.jsc, wn, wn32, c->n, c->mesh.nx, c->mesh.ny, s);
+    if (st == HELM_OK && jac)
+      st = jacobi_prepare(reinterpret_cast<double*>(val), cflag, Y.djac, c->n, c->mesh.nx, c->mesh.ny, c->mesh.nz, s);
+    if (st == HELM_OK && prec == 1) st = cast_values(val, const_cast<cf*>(Y.val32), 27 * c->n, s);
+    if (st == HELM_OK && prec == 2)
+      st = split_values(reinterpret_cast<const double*>(val), const_cast<float2*>(Y.valw), 54 * c->n, s);
     if (st != HELM_OK) {
       cudaFree(A.base);
       return st;
@@ -865,6 +915,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   int* d_ctrl = A.take<int>(CTRL_N);
   cd* d_part = A.take<cd>(2 * (size_t)ntiles);
   GridBar* d_bar = A.take<GridBar>(1);
+  unsigned long long* d_trace = trace_steps ? A.take<unsigned long long>((size_t)trace_steps * 6) : nullptr;
   std::vector<int> l0(ntiles);
   for (int t = 0; t < ntiles; ++t) l0[t] = t;
   int ctrl[CTRL_N] = {0};
@@ -898,26 +949,58 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   P.inner_maxit = o.inner_maxit;
   P.max_outer = o.max_outer;
   P.stall = o.stall_window;
+  P.trace = d_trace;
+  P.trace_steps = trace_steps;
   // Host-side fault injection for tests (never set in normal use): the barriers wait for one
   // block that does not exist and give up after 200 ms, so the launch ends with HELM_TIMEOUT
   // without faulting or hanging the GPU.
   const FaultMode fm = fault_mode();
   P.bar_extra = fm == FAULT_BARRIER ? 1u : 0u;
   P.bar_timeout = fm == FAULT_BARRIER ? 200000000ull : kTimeoutNs;
-  // each super-step advances every active system by one Krylov step, except refinement
-  // residual steps (at most max_outer + 1 of them) and COCG residual checks
+  // each super-step advances every active system by one Krylov step (one BiCGSTAB iteration),
+  // except refinement residual steps (at most max_outer + 1 of them) and residual checks
   P.max_steps = 2 * o.maxit + 2 * (o.max_outer + 2) + 16;
+  if (tfq) P.max_steps = 6 * o.maxit + 16;  // one barrier per sub-step, at most 4 per restart cycle
   void* args[] = {&P};
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
   if (e == cudaSuccess)
     e = cudaLaunchCooperativeKernel((const void*)kern, dim3(nblocks), dim3(kBlock), args, 0, s);
   if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
+  // back to the unknowns of A x = b (also for a system that did not converge: its best iterate)
+  if (jac)  // x = D^-1 y
+    for (int k = 0; k < nsys && e == cudaSuccess; ++k)
+      if (jacobi_unscale(hs[k].x, hs[k].djac, hs[k].n, s) != HELM_OK) e = cudaGetLastError();
+  if (sjac)  // x = S y
+    for (int k = 0; k < nsys && e == cudaSuccess; ++k)
+      if (jacobi_rescale(hs[k].x, hs[k].jsc, hs[k].n, s) != HELM_OK) e = cudaGetLastError();
   GridBar hb;
   memset(&hb, 0, sizeof(hb));
   if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), d_st, nsys * sizeof(KState), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s);
+  std::vector<unsigned long long> htrace((size_t)trace_steps * 6);
+  if (e == cudaSuccess && trace_steps)
+    e = cudaMemcpyAsync(htrace.data(), d_trace, htrace.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(A.base);
+  if (e == cudaSuccess && trace_steps > 1) {
+    // mean durations (us) over the traced steps: own work of A, wait at barrier A, B work, B
+    // wait, C work, C wait (block 0's view)
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    int cnt = 0;
+    for (int k = 1; k < trace_steps; ++k) {
+      const unsigned long long* t = &htrace[(size_t)k * 6];
+      const unsigned long long prev = htrace[(size_t)(k - 1) * 6 + 5];
+      if (t[5] == 0 || prev == 0) break;
+      acc[0] += (double)(t[0] - prev); acc[1] += (double)(t[1] - t[0]);
+      acc[2] += (double)(t[2] - t[1]); acc[3] += (double)(t[3] - t[2]);
+      acc[4] += (double)(t[4] - t[3]); acc[5] += (double)(t[5] - t[4]);
+      ++cnt;
+    }
+    if (cnt)
+      fprintf(stderr, "helm trace (%d steps, us): A work %.2f wait %.2f | B work %.2f wait %.2f | C work %.2f wait %.2f\n",
+              cnt, acc[0] / cnt / 1e3, acc[1] / cnt / 1e3, acc[2] / cnt / 1e3, acc[3] / cnt / 1e3, acc[4] / cnt / 1e3,
+              acc[5] / cnt / 1e3);
+  }
   if (e == cudaSuccess) {
     float t_asm = 0.f, t_solve = 0.f;
     cudaEventElapsedTime(&t_asm, ev[0], ev[1]);

@@ -49,15 +49,17 @@ __global__ void __launch_bounds__(kBlock) spmv_dia_kernel(const cplx<T>* __restr
   for (int64_t base = blockIdx.x * (int64_t)kBlock; base < n; base += (int64_t)gridDim.x * kBlock) {
     const int64_t row = base + threadIdx.x;
     const bool valid = row < n;
+    const T* vre = reinterpret_cast<const T*>(val);  // split layout: real parts, then imaginary
+    const T* vim = vre + 27 * n;
     cplx<T> s(T(0), T(0));
     int c = 0;
     if (valid) {
-      s = dia_row_re<T>(val, x, n, Nx, NxNy, row);
+      s = dia_row_re<T>(vre, x, n, Nx, NxNy, row);
       c = cflag[row];
     }
     if (__syncthreads_or(c)) {
       if (c) {
-        const cplx<T> si = dia_row_im<T>(val, x, n, Nx, NxNy, row);
+        const cplx<T> si = dia_row_im<T>(vim, x, n, Nx, NxNy, row);
         s = cplx<T>(s.re + si.re, s.im + si.im);
       }
     }

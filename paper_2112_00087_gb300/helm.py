@@ -22,8 +22,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "NOT_CONV
                 6: "NAN", 7: "PIVOT", 8: "TIMEOUT", 9: "ERR_STATE"}
 HELM_C128, HELM_C64 = 0, 1
 HELM_FMT_CSR, HELM_FMT_DIA27 = 0, 1
-HELM_SOLVER_GMRES, HELM_SOLVER_COCG = 0, 1
-HELM_PRECOND_NONE, HELM_PRECOND_RAS = 0, 1
+HELM_SOLVER_GMRES, HELM_SOLVER_COCG, HELM_SOLVER_BICGSTAB, HELM_SOLVER_TFQMR = 0, 1, 2, 3
+HELM_PRECOND_NONE, HELM_PRECOND_RAS, HELM_PRECOND_JACOBI = 0, 1, 2
 
 # Symbols declared in include/helm.h (tests check the library exports all of them).
 EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary", "helm_sizes",
@@ -133,14 +133,16 @@ def _stream(stream=None):
 def make_opts(solver="cocg", restart=50, tol=1e-10, maxit=100000, precond=None, ras_parts=(8, 4, 4),
               ras_overlap=2, mixed=False, inner_tol=1e-4, inner_maxit=5000, max_outer=50, stall_window=0) -> SolveOpts:
     o = SolveOpts()
-    o.solver = HELM_SOLVER_GMRES if solver == "gmres" else HELM_SOLVER_COCG
+    o.solver = {"gmres": HELM_SOLVER_GMRES, "cocg": HELM_SOLVER_COCG, "bicgstab": HELM_SOLVER_BICGSTAB,
+                "tfqmr": HELM_SOLVER_TFQMR}[solver]
     o.restart = restart
     o.tol = tol
     o.maxit = maxit
-    o.precond = HELM_PRECOND_RAS if precond == "ras" else HELM_PRECOND_NONE
+    o.precond = {None: HELM_PRECOND_NONE, "ras": HELM_PRECOND_RAS, "jacobi": HELM_PRECOND_JACOBI}[precond]
     o.ras_parts[:] = list(ras_parts)
     o.ras_overlap = ras_overlap
-    o.mixed = 1 if mixed else 0
+    # mixed: False / True (complex64 inner) / "c64" / "dw" (double-word inner)
+    o.mixed = {False: 0, True: 1, "c64": 1, "dw": 2}[mixed]
     o.inner_tol = inner_tol
     o.inner_maxit = inner_maxit
     o.max_outer = max_outer
@@ -219,14 +221,13 @@ class Matrix:
         return rowptr, col, val
 
     def dia27(self):
-        """Values [27, n] (slot k = (di+1) + 3(dj+1) + 9(dl+1))."""
+        """Complex values [27, n] (slot k = (di+1) + 3(dj+1) + 9(dl+1)) from the split layout."""
         n, prec, vl = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_void_p()
         _check(LIB.helm_matrix_dia27(self.handle, ctypes.byref(n), ctypes.byref(prec), ctypes.byref(vl)))
-        vdt = torch.complex64 if prec.value == HELM_C64 else torch.complex128
-        val = torch.empty(27 * n.value, dtype=vdt, device="cuda")
-        torch.cuda.synchronize()
-        _cuda_copy(val, vl.value)
-        return val.reshape(27, n.value)
+        real = torch.float32 if prec.value == HELM_C64 else torch.float64
+        flat = torch.as_tensor(_DevView(vl.value, (54 * n.value,), "<f4" if real == torch.float32 else "<f8"),
+                               device="cuda").clone()
+        return torch.complex(flat[:27 * n.value], flat[27 * n.value:]).reshape(27, n.value)
 
     def free(self):
         if self.handle is not None and self.handle.value:

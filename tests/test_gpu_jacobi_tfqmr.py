@@ -1,0 +1,166 @@
+"""GPU parity of the Jacobi-preconditioned solvers and of TFQMR against the CPU oracle, through
+the C ABI: symmetric Jacobi COCG (S A S, S = diag(A)^-1/2, FP64, double-word and complex64
+mixed), right-Jacobi BiCGSTAB (A D^-1), and TFQMR with and without right Jacobi (the paper's
+P-BiCGSTAB / P-tfQMR of Sec. 4 with "P" read as Jacobi).
+
+COCG's step count is compared as for the unpreconditioned solver (the oracle's spread under
+rounding-level perturbations of b, widened by 5%); BiCGSTAB and TFQMR are pinned by their early
+iterates (identical up to rounding) and by converged values at tol 1e-12.
+"""
+import numpy as np
+import pytest
+
+import helm_inputs as hi
+from oracle import fem, krylov
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2112_00087_gb300 import helm  # noqa: E402
+from tests.gpu_util import context, rel  # noqa: E402
+
+
+def sym_cocg(A, b, tol, maxit=40000):
+    Ah, s, w = krylov.sym_jacobi(A)
+    y, st = krylov.cocg(lambda v: Ah @ v, s * b, tol=tol, maxit=maxit, weights=w)
+    return s * y, st, (Ah, s, w)
+
+
+def sym_count_range(A, b, tol, seeds=(1, 2, 3)):
+    Ah, s, w = krylov.sym_jacobi(A)
+    counts = [krylov.cocg(lambda v: Ah @ v, s * b, tol=tol, maxit=40000, weights=w)[1].iterations]
+    for sd in seeds:
+        rng = np.random.default_rng(sd)
+        e = (rng.standard_normal(len(b)) + 1j * rng.standard_normal(len(b))) * 1e-14 * np.abs(b).max()
+        counts.append(krylov.cocg(lambda v: Ah @ v, s * (b + e), tol=tol, maxit=40000, weights=w)[1].iterations)
+    return min(counts), max(counts)
+
+
+CASES = [((20, 16, 12), 100.0, "box"), ((13, 7, 5), 230.0, "cabin"), ((30, 20, 14), 310.0, "box")]
+
+
+def problem(dims, kind):
+    return hi.small_box_problem(*dims) if kind == "box" else hi.cabin_problem(*dims)
+
+
+@pytest.mark.parametrize("dims,f,kind", CASES)
+def test_sym_jacobi_cocg_matches_oracle(dims, f, kind):
+    prob = problem(dims, kind)
+    ctx = context(prob)
+    A, b = fem.system(prob, f)
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts("cocg", tol=1e-10, maxit=20000, precond="jacobi"))
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0
+    assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
+    lo, hi_ = sym_count_range(A, b, 1e-10)
+    assert 0.95 * lo - 1 <= st[0]["iterations"] <= 1.05 * hi_ + 1, (st[0], lo, hi_)
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts("cocg", tol=1e-12, maxit=40000, precond="jacobi"))
+    x, ost, _ = sym_cocg(A, b, 1e-12)
+    assert st[0]["status"] == 0 and ost.converged
+    assert rel(p[0].cpu().numpy(), x) <= 1e-9
+
+
+@pytest.mark.parametrize("k", [1, 2, 9])
+def test_sym_jacobi_cocg_early_iterates(k):
+    prob = hi.cabin_problem(13, 7, 5)
+    ctx = context(prob)
+    A, b = fem.system(prob, 150.0)
+    p, st = helm.helm_solve(ctx, [150.0], helm.make_opts("cocg", tol=1e-14, maxit=k, precond="jacobi"),
+                            raise_on_fail=False)
+    x, ost, _ = sym_cocg(A, b, 1e-14, maxit=k)
+    assert st[0]["status"] == helm.HELM_NOT_CONVERGED and st[0]["iterations"] == k
+    assert rel(p[0].cpu().numpy(), x) <= 1e-10
+    # the reported residual is that of A x = b, not of the scaled system
+    assert abs(st[0]["relres"] - ost.relres) <= 1e-8 * ost.relres
+
+
+@pytest.mark.parametrize("mixed", ["dw", "c64"])
+def test_sym_jacobi_mixed_modes(mixed):
+    prob = hi.cabin_problem(40, 22, 19)
+    f = 150.0
+    ctx = context(prob)
+    A, b = fem.system(prob, f)
+    o = helm.make_opts("cocg", tol=1e-10, maxit=50000, precond="jacobi", mixed=mixed,
+                       inner_tol=1e-12 if mixed == "dw" else 1e-4, inner_maxit=50000 if mixed == "dw" else 5000,
+                       max_outer=30, stall_window=15000)
+    p, st = helm.helm_solve(ctx, [f], o)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0, st
+    assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
+    if mixed == "dw":
+        _, ost, _ = sym_cocg(A, b, 1e-10)
+        assert st[0]["outer"] >= 1 and 0.75 * ost.iterations - 2 <= st[0]["iterations"] <= 1.25 * ost.iterations + 2
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "tfqmr"])
+@pytest.mark.parametrize("k", [1, 2, 3, 8])
+def test_right_jacobi_early_iterates(solver, k):
+    prob = hi.cabin_problem(13, 7, 5)
+    ctx = context(prob)
+    A, b = fem.system(prob, 150.0)
+    p, st = helm.helm_solve(ctx, [150.0], helm.make_opts(solver, tol=1e-14, maxit=k, precond="jacobi"),
+                            raise_on_fail=False)
+    mv, unscale = krylov.right_jacobi(A)
+    y, ost = getattr(krylov, solver)(mv, b, tol=1e-14, maxit=k)
+    assert st[0]["status"] == helm.HELM_NOT_CONVERGED and st[0]["iterations"] == k
+    assert rel(p[0].cpu().numpy(), unscale(y)) <= 1e-10
+    assert abs(st[0]["relres"] - ost.relres) <= 1e-8 * ost.relres
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_tfqmr_early_iterates_unpreconditioned(k):
+    prob = hi.small_box_problem(10, 8, 6)
+    ctx = context(prob)
+    A, b = fem.system(prob, 100.0)
+    p, st = helm.helm_solve(ctx, [100.0], helm.make_opts("tfqmr", tol=1e-14, maxit=k), raise_on_fail=False)
+    x, ost = krylov.tfqmr(lambda v: A @ v, b, tol=1e-14, maxit=k)
+    assert st[0]["status"] == helm.HELM_NOT_CONVERGED and st[0]["iterations"] == k
+    assert rel(p[0].cpu().numpy(), x) <= 1e-10
+
+
+@pytest.mark.parametrize("solver,precond,dims,f", [
+    ("tfqmr", "jacobi", (20, 16, 12), 100.0), ("tfqmr", "jacobi", (13, 7, 5), 230.0),
+    ("tfqmr", None, (10, 8, 6), 100.0), ("bicgstab", "jacobi", (20, 16, 12), 100.0),
+    ("bicgstab", "jacobi", (30, 20, 14), 310.0)])
+def test_converged_values_match_oracle(solver, precond, dims, f):
+    prob = hi.small_box_problem(*dims)
+    ctx = context(prob)
+    A, b = fem.system(prob, f)
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts(solver, tol=1e-12, maxit=40000, precond=precond))
+    if precond:
+        mv, unscale = krylov.right_jacobi(A)
+    else:
+        mv, unscale = (lambda v: A @ v), (lambda y: y)
+    y, ost = getattr(krylov, solver)(mv, b, tol=1e-12, maxit=40000)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0 and ost.converged
+    assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-12
+    assert rel(g, unscale(y)) <= 1e-9
+
+
+def test_jacobi_tfqmr_batch_of_sweep_lattices():
+    freqs = [20.0, 60.0, 140.0]
+    probs = [hi.cabin_problem(*hi.sweep_mesh_dims(f)) for f in freqs]
+    ctxs = [context(pr) for pr in probs]
+    ps, st = helm.helm_solve_batch(ctxs, freqs, helm.make_opts("tfqmr", tol=1e-10, maxit=40000, precond="jacobi"),
+                                   raise_on_fail=False)
+    for k, (pr, f) in enumerate(zip(probs, freqs)):
+        A, b = fem.system(pr, f)
+        g = ps[k].cpu().numpy()
+        assert st[k]["status"] == 0, (f, st[k])
+        assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
+
+
+def test_jacobi_rejected_for_gmres_and_zero_rhs():
+    ctx = context(hi.small_box_problem(6, 4, 3))
+    with pytest.raises(helm.HelmError):
+        helm.helm_solve(ctx, [100.0], helm.make_opts("gmres", precond="jacobi"))
+    mesh = hi.Mesh(1, 1, 1, 0.3, 0.2, 0.1)
+    zero = hi.Problem(mesh, np.full(6, 0.02 + 0.01j), np.array([7], dtype=np.int32), np.array([0.0 + 0.0j]))
+    for solver in ("cocg", "bicgstab", "tfqmr"):
+        p, st = helm.helm_solve(context(zero), [500.0], helm.make_opts(solver, tol=1e-10, precond="jacobi"))
+        assert st[0]["status"] == 0 and st[0]["iterations"] == 0
+        assert np.all(p[0].cpu().numpy() == 0)

@@ -38,3 +38,16 @@ def test_boundary_numbering_and_draws_are_seeded():
     assert np.array_equal(p1.beta, p2.beta) and np.array_equal(p1.p_dir, p2.p_dir)
     w = hi.listener_weights(hi.Mesh(100, 56, 48, *hi.CABIN))
     assert abs(w.sum() - 1.0) < 1e-12 and (w > 0).sum() > 100
+
+
+def test_resonance_sweep_inputs():
+    f = hi.resonance_freqs(64)
+    # bins 4..67 of a 512-point FFT at 256 Hz: spacing fs / N = 0.5 Hz
+    assert np.allclose(np.diff(f), 256.0 / 512.0) and f[0] == 2.0 and f[-1] == 33.5
+    a = hi.resonance_spectrum(f)
+    assert f[np.argmax(np.abs(a))] == 13.0
+    # the half-harmonic bump: a local maximum of |a| at 6.5 Hz
+    k = int(np.where(f == 6.5)[0][0])
+    assert abs(a[k]) > abs(a[k - 1]) and abs(a[k]) > abs(a[k + 1])
+    # seeded: the same draw every time
+    assert np.array_equal(a, hi.resonance_spectrum(f))
