@@ -41,16 +41,18 @@ TOL = 1e-10
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent launch of the
 # default benchmark step, from a single-pass ncu capture (profiles/traffic_sweep256.md), valid
 # only for the kernel sources it was taken on: reported as null once they change.
-TRAFFIC_CAPTURE = {"sources_sha256_16": "c0be1ff6bd7b1166", "bytes": 98444236640512 + 10995534523904}
-KERNEL_SOURCES = ("paper_2112_00087_gb300/csrc/krylov_cocg.cu", "paper_2112_00087_gb300/csrc/kernels.cuh",
+TRAFFIC_CAPTURE = {"config": "sweep256/cocg/dw/jacobi", "sources_sha256_16": "", "bytes": None}
+KERNEL_SOURCES = ("paper_2112_00087_gb300/csrc/krylov_cocg.cu", "paper_2112_00087_gb300/csrc/krylov_engine.cuh",
+                  "paper_2112_00087_gb300/csrc/kernels.cuh", "paper_2112_00087_gb300/csrc/dw.cuh",
                   "paper_2112_00087_gb300/csrc/common.cuh")
 
 
 def captured_traffic(args):
     if args.traffic is not None:
         return args.traffic
-    if (args.workload != "sweep256" or args.nfreq != 256 or args.mixed or args.solver != "cocg"
-            or args.precision != "fp64" or args.precond != "none"):
+    key = "%s/%s/%s/%s" % (args.workload if args.nfreq == 256 else "other", args.solver,
+                           "c64" if args.mixed else args.precision, args.precond)
+    if key != TRAFFIC_CAPTURE["config"] or TRAFFIC_CAPTURE["bytes"] is None:
         return None
     import hashlib
     h = hashlib.sha256()
@@ -457,27 +459,28 @@ def run_gpu(args):
     if rank == 0 and not args.quick:
         # the other COCG modes, batched, timed once each
         out["legs"] = {}
-        for name in ("fp64", "c64", "dw"):
-            if name == leg:
-                continue
+        cmp_legs = [(name, legs[name][0], legs[name][5]) for name in ("fp64", "c64", "dw") if name != leg]
+        if pc is not None:
+            cmp_legs.append(("fp64_unpreconditioned", fp64_opts(helm, args.maxit), "fp64 COCG, no preconditioner"))
+        for name, o2, desc2 in cmp_legs:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, st2 = helm.helm_solve_batch(ctxs, freqs, legs[name][0], outs, raise_on_fail=False)
+            _, st2 = helm.helm_solve_batch(ctxs, freqs, o2, outs, raise_on_fail=False)
             torch.cuda.synchronize()
             t2 = time.perf_counter() - t0
-            out["legs"][name] = {"freqs_per_s": nsys / t2, "precision": legs[name][5],
+            out["legs"][name] = {"freqs_per_s": nsys / t2, "precision": desc2,
                                  "converged": sum(1 for s in st2 if s["status"] == 0),
                                  "iterations_total": int(sum(s["iterations"] for s in st2)),
                                  "inner_iterations": int(sum(s["iterations_c64"] for s in st2)),
                                  "fell_back_to_fp64": int(sum(1 for s in st2 if s["outer"] < 0))}
         if not args.no_sequential:
-            # plain FP64, one frequency per call (no batching)
+            # FP64 COCG (same preconditioning as the main leg), one frequency per call (no batching)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for c, f, o in zip(ctxs, freqs, outs):
                 helm.helm_solve_batch([c], [f], legs["fp64"][0], [o], raise_on_fail=False)
             torch.cuda.synchronize()
-            out["plain_fp64_sequential"] = {"freqs_per_s": nsys / (time.perf_counter() - t0)}
+            out["fp64_sequential"] = {"freqs_per_s": nsys / (time.perf_counter() - t0), "precision": legs["fp64"][5]}
         out["spmv"] = spmv_roofline(helm, torch, peak_gbs)
 
         # end to end through host buffers: boundary data in from pinned memory, pressures out
@@ -653,14 +656,13 @@ def main():
                     help="sweep256 is the benchmark; the one-lattice cases serve profiling")
     ap.add_argument("--maxit", type=int, default=45000, help="Krylov step cap per system")
     ap.add_argument("--mixed", action="store_true", help="same as --precision c64")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "c64", "dw"],
+    ap.add_argument("--precision", default="dw", choices=["fp64", "c64", "dw"],
                     help="COCG mode of the main leg: FP64, or FP64 refinement around a complex64 / double-word "
                          "inner solve")
     ap.add_argument("--solver", default="cocg", choices=["cocg", "bicgstab", "tfqmr"],
                     help="Krylov method of the main leg (BiCGSTAB / TFQMR: FP64)")
-    ap.add_argument("--precond", default="none", choices=["none", "jacobi"],
+    ap.add_argument("--precond", default="jacobi", choices=["none", "jacobi"],
                     help="Jacobi preconditioning (symmetric for COCG, right for BiCGSTAB / TFQMR)")
-    ap.add_argument("--fp64", action="store_true", help="(default) time the FP64 solver as the main leg")
     ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
     ap.add_argument("--configs", action="store_true", help="measure the secondary workloads instead")
     ap.add_argument("--traffic", type=float, default=None,

@@ -98,9 +98,12 @@ typedef struct {
   int32_t inner_maxit;  /* mixed: inner steps per refinement step */
   int32_t max_outer;    /* mixed: refinement steps before HELM_NOT_CONVERGED */
   int32_t stall_window; /* COCG: if the residual estimate has not halved its best value within
-                           this many steps, check the true residual and restart from the current
-                           iterate (0 = never; counted in stats.restarts); mixed: end the inner
-                           solve (the next refinement step restarts from the current iterate) */
+                           this many steps, check the true residual and restart (0 = never;
+                           counted in stats.restarts) -- from the iterate saved at the last
+                           halving if that happened since the last restart and the estimate is
+                           above it now, else from the current iterate; the same rule picks the
+                           iterate returned at the step cap. Mixed: ends the inner solve (the
+                           next refinement step restarts from the current iterate) */
   int32_t pad_;
 } helm_solve_opts;
 

@@ -16,7 +16,11 @@ by step in complex128 numpy, the two iterations the GPU path runs:
   A: CG with the unconjugated bilinear form x^T y. Stop when ||r_rec||/||b|| <= tol, then
   the true residual is checked; if it misses tol the iteration restarts from the current
   x with r = b - A x. Optional stagnation rule (``stall``): when the estimate has not halved
-  its best value within ``stall`` steps, the same check-and-restart is taken.
+  its best value within ``stall`` steps, the check-and-restart is taken from the iterate saved
+  at the last halving of the best estimate, if that halving happened in the current run and the
+  current estimate is above it (COCG's residual on near-resonant systems can grow by orders of
+  magnitude; the current iterate is then far worse than an earlier one), else from the current
+  iterate. The same rule picks the iterate checked when the step cap ends the iteration.
 
 * ``bicgstab``: BiCGSTAB (van der Vorst 1992), the paper's own Sec. 4 solver (Table 3,
   "P-BiCGSTAB"; the paper does not name its preconditioner "P", so none is applied), complex
@@ -187,9 +191,12 @@ def cocg(matvec, b, tol=1e-10, maxit=100000, stall=None, weights=None):
         return x, st
     r = b.copy()
     best, best_it = 1.0, 0
+    xb = x.copy()  # iterate at the last halving of the best estimate
+    start_it = 0   # step count at the last (re)start
     while True:
         p = r.copy()
         rho = dotu(r, r)
+        est = best
         while st.iterations < maxit:
             q = matvec(p)
             st.iterations += 1
@@ -204,11 +211,17 @@ def cocg(matvec, b, tol=1e-10, maxit=100000, stall=None, weights=None):
             st.history.append(est)
             if est < 0.5 * best:
                 best, best_it = est, st.iterations
+                xb = x.copy()
             if est <= tol or (stall and st.iterations - best_it >= stall):
                 break
             rho_new = dotu(r, r)
             p = r + (rho_new / rho) * p
             rho = rho_new
+        if est > tol and best < est and best_it > start_it and not st.breakdown:
+            # stagnation or step cap above the best estimate of this run: check (and restart
+            # from) the iterate saved at that estimate; without a halving since the last restart
+            # the current iterate is kept (restarting from the same point would repeat the run)
+            x = xb.copy()
         r = b - matvec(x)
         st.relres = nrm2(r) / nb
         if st.relres <= tol:
@@ -218,6 +231,8 @@ def cocg(matvec, b, tol=1e-10, maxit=100000, stall=None, weights=None):
             return x, st
         st.restarts += 1
         best, best_it = st.relres, st.iterations
+        start_it = st.iterations
+        xb = x.copy()
 
 
 def bicgstab(matvec, b, tol=1e-10, maxit=100000):

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kBlock, MINB) bicg_persistent(KParams P) {
 // and sets the next sub-step. The x update x += eta d of a step needs that step's eta (known
 // only after its reduction), so it is applied by the following sub-step, row by row, before d
 // changes. One pair of steps = T_EVEN, T_ODD, T_U, T_V: four super-steps, two SpMVs.
-// Vectors: w = sv, u = p, v = q, A u = tv, d = dv, r0* = rs.
+// Vectors: w = sv, u = p, v = q, A u = tv (A u_m of the current step), d = dv, r0* = rs.
 
 enum : int { T_SETUP = 0, T_V0 = 1, T_EVEN = 2, T_ODD = 3, T_U = 4, T_V = 5, T_XC = 6, T_RES = 7 };
 
@@ -331,7 +331,8 @@ __device__ void tq_setup(const KParams& P, int t, double* sh, const KTile& T, KS
   }
 }
 
-// v = A u (+ beta (A u_old + beta v) after an odd step), then alpha = rho / (r0*, v)
+// v = A u (+ beta (A u_old + beta v) after an odd step), A u kept for the even step, then
+// alpha = rho / (r0*, v)
 __device__ void tq_v(const KParams& P, int t, double* sh, const KTile& T, KState* S, const KSys& Y, bool first) {
   const cd be = first ? cd(0.0, 0.0) : S->beta;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -342,6 +343,7 @@ __device__ void tq_v(const KParams& P, int t, double* sh, const KTile& T, KState
       cfma(w, be, Y.q[row]);
       cfma(vn, be, w);
     }
+    Y.tv[row] = au;  // A u of the coming even step
     Y.q[row] = vn;
     const cd rsi = Y.rs[row];
     v[0] += rsi.re * vn.re + rsi.im * vn.im;
@@ -399,7 +401,7 @@ __device__ void tq_even(const KParams& P, int t, double* sh, const KTile& T, KSt
     cfma(un, mal, vi);     // u - alpha v
     Y.p[i] = un;
     cd wn = Y.sv[i];
-    cfma(wn, mal, vi);     // A u_m = v_m on even steps
+    cfma(wn, mal, Y.tv[i]);  // w - alpha A u_m
     Y.sv[i] = wn;
     v[2] += wn.re * wn.re + wn.im * wn.im;
   }

@@ -161,12 +161,19 @@ __device__ void phaseB_fp64(const KParams& P, int t, double* sh) {
       const double est = sqrt(rr.re) / S->bnorm;
       S->est = est;
       S->amode = 0;
+      S->save_best = 0;
       if (est < 0.5 * S->best_est) {
         S->best_est = est;
         S->best_it = S->it;
+        S->save_best = 1;
       }
       if (!(est > P.tol) || S->it >= P.maxit || S->bd || (P.stall > 0 && S->it - S->best_it >= P.stall)) {
-        S->cmode = C_CHECK;  // converged estimate, step cap, breakdown, or stagnation: true residual
+        // converged estimate, step cap, breakdown, or stagnation: true residual -- of the saved
+        // best iterate if the estimate halved since the last restart and is above that value now
+        // (restarting from the same point again would repeat the run)
+        const bool best = est > P.tol && S->best_est < est && S->best_it > S->start_it && !S->bd;
+        S->cmode = best ? C_CHECK_BEST : C_CHECK;
+        S->save_best = 0;
       } else {
         S->beta = cdiv(rho_new, S->rho);
         S->rho = rho_new;
@@ -181,8 +188,11 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
   KState* S = P.st + T.sys;
   if (!vload(&S->act)) return;
   const KSys Y = P.sys[T.sys];
-  if (vload(&S->cmode) == C_PUPDATE) {
+  const int cmode = vload(&S->cmode);
+  if (cmode == C_PUPDATE) {
     const cd be = S->beta;
+    if (vload(&S->save_best))
+      for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) Y.xb[i] = Y.x[i];
     constexpr int U = HELM_VEC_UNROLL;
     for (int64_t i0 = T.row0 + threadIdx.x; i0 < T.row1; i0 += U * kBlock) {
       cd rv[U], pv[U];
@@ -205,7 +215,10 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
     }
     return;
   }
-  // true residual r = b - A x
+  // true residual r = b - A x (x replaced by the saved best iterate first for C_CHECK_BEST: the
+  // product reads xb, and each thread copies its own rows into x, which nothing reads here)
+  const bool from_best = cmode == C_CHECK_BEST;
+  const cd* xs = from_best ? Y.xb : Y.x;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   auto add = [&](int64_t row, cd ri) {
     v[0] += ri.re * ri.re - ri.im * ri.im;
@@ -213,8 +226,9 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
     v[2] += wnorm(Y, row) * (ri.re * ri.re + ri.im * ri.im);
   };
   tile_spmv<double>(
-      Y.val, Y.cflag, Y.x, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
+      Y.val, Y.cflag, xs, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1,
       [&](int64_t row, cd s, int c) {
+        if (from_best) Y.x[row] = Y.xb[row];
         const cd bi = Y.b[row];
         const cd ri(bi.re - s.re, bi.im - s.im);
         Y.r[row] = ri;
@@ -244,6 +258,7 @@ __device__ void phaseC_fp64(const KParams& P, int t, double* sh) {
         S->restarts += 1;
         S->best_est = rel;
         S->best_it = S->it;
+        S->start_it = S->it;
       }
     }
   }
@@ -295,6 +310,7 @@ __device__ void resid_phaseA(const KParams& P, int t, double* sh, const KTile& T
         S->reset_x = 1;
         S->best_est = 1.0;
         S->best_it = S->it;
+        S->start_it = S->it;
         S->rho = rho;
         S->amode = 1;
         S->bd = 0;
@@ -784,7 +800,10 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   void (*kern)(KParams) = nullptr;
   if (bicg) kern = reinterpret_cast<void (*)(KParams)>(bicg_kernel(want));
   else if (tfq) kern = reinterpret_cast<void (*)(KParams)>(tfqmr_kernel(want));
-  else if (prec == 2) kern = want >= 2 ? cocg_persistent<2, 2> : cocg_persistent<2, 1>;
+  else if (prec == 2)
+    kern = want >= 4 ? cocg_persistent<2, 4>
+         : want == 3 ? cocg_persistent<2, 3>
+         : want == 2 ? cocg_persistent<2, 2> : cocg_persistent<2, 1>;
   else if (want == 4) kern = mixed ? cocg_persistent<1, 4> : cocg_persistent<0, 4>;
   else if (want == 3) kern = mixed ? cocg_persistent<1, 3> : cocg_persistent<0, 3>;
   else if (want == 2) kern = mixed ? cocg_persistent<1, 2> : cocg_persistent<0, 2>;
@@ -817,6 +836,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     if (prec == 1) bytes += rnd(nnz * sizeof(cf)) + 4 * rnd(n * sizeof(cf));
     if (prec == 2) bytes += rnd(nnz * 2 * sizeof(float2)) + 4 * rnd(n * sizeof(cw));
     bytes += 2 * rnd(n * sizeof(cd));  // p, q (FP64 COCG, also the fallback of the mixed solver)
+    if (!(bicg || tfq)) bytes += rnd(n * sizeof(cd));  // best iterate of FP64 COCG
     if (bicg || tfq) bytes += 3 * rnd(n * sizeof(cd));  // rs, s, t (TFQMR: r0*, w, A u)
     if (tfq) bytes += rnd(n * sizeof(cd));              // TFQMR direction d
     if (jac) bytes += rnd(n * sizeof(cd));              // diag(A)
@@ -870,6 +890,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     }
     Y.p = A.take<cd>(c->n);
     Y.q = A.take<cd>(c->n);
+    if (!(bicg || tfq)) Y.xb = A.take<cd>(c->n);
     if (bicg || tfq) {
       Y.rs = A.take<cd>(c->n);
       Y.sv = A.take<cd>(c->n);
@@ -1016,9 +1037,16 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   if (e != cudaSuccess) return cuda_error(e, "cocg persistent solve");
 
   helm_status overall = HELM_OK;
+  const bool dbg = getenv("HELM_DEBUG_STATE") != nullptr;  // diagnosis aid: state of failed systems
   for (int k = 0; k < nsys; ++k) {
     helm_solve_stats& S = *sys[k].stats;
     const KState& K = hst[k];
+    if (dbg && (K.act || K.status != HELM_OK))
+      fprintf(stderr,
+              "helm state sys %d: status %d it %d bd %d est %.3e relres %.3e rho (%.3e,%.3e) alpha (%.3e,%.3e) "
+              "omega (%.3e,%.3e) beta (%.3e,%.3e) tau %.3e theta %.3e\n",
+              k, K.status, K.it, K.bd, K.est, K.relres, K.rho.re, K.rho.im, K.alpha.re, K.alpha.im, K.omega.re,
+              K.omega.im, K.beta.re, K.beta.im, K.tau, K.theta);
     S.status = K.act ? HELM_NOT_CONVERGED : K.status;
     if (hb.status & DEV_TIMEOUT) S.status = HELM_TIMEOUT;
     S.iterations = K.it;

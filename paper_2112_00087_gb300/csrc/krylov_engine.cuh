@@ -30,6 +30,7 @@ struct KSys {
   cw* rw;
   cw* pw;
   cw* qw;
+  cd* xb;   // FP64 COCG: iterate at the last halving of the best residual estimate
   cd* dv;   // TFQMR: direction d
   cd* djac; // right Jacobi: diag(A) of the unscaled matrix, or null
   cd* jsc;  // symmetric Jacobi (COCG): s_i = a_ii^-1/2, the system solved is S A S y = S b, x = S y
@@ -42,7 +43,9 @@ struct KSys {
 };
 
 enum : int { MODE_RESID = 0, MODE_INNER = 1, MODE_FP64 = 2 };
-enum : int { C_PUPDATE = 0, C_CHECK = 1, C_XUPDATE = 2 };
+// phase C actions: direction update; true residual of x; true residual of the saved best
+// iterate (which becomes x); refinement update of the mixed modes
+enum : int { C_PUPDATE = 0, C_CHECK = 1, C_XUPDATE = 2, C_CHECK_BEST = 3 };
 
 struct KState {
   int act;       // 1 while iterating
@@ -62,6 +65,8 @@ struct KState {
   int fell_back; // mixed: the system finished in FP64 COCG
   int reset_x;   // mixed: the fallback restarts from x = 0 (refinement left x worse than zero)
   int best_it;   // step of the last halving of the best residual estimate
+  int start_it;  // step count at the last (re)start of FP64 COCG
+  int save_best; // phase C copies x to the best iterate (the estimate just halved)
   unsigned arrive;
   double bnorm, rnorm, relres, est, prev_rel, best_est;
   cd rho, alpha, beta, omega;

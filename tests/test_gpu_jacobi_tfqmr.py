@@ -5,10 +5,12 @@ P-BiCGSTAB / P-tfQMR of Sec. 4 with "P" read as Jacobi).
 
 COCG's step count is compared as for the unpreconditioned solver (the oracle's spread under
 rounding-level perturbations of b, widened by 5%); BiCGSTAB and TFQMR are pinned by their early
-iterates (identical up to rounding) and by converged values at tol 1e-12.
+iterates (identical up to rounding) and by converged results at tol 1e-12 that are as close to
+x* = A^-1 b as the oracle's.
 """
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spl
 
 import helm_inputs as hi
 from oracle import fem, krylov
@@ -95,13 +97,17 @@ def test_sym_jacobi_mixed_modes(mixed):
         assert st[0]["outer"] >= 1 and 0.75 * ost.iterations - 2 <= st[0]["iterations"] <= 1.25 * ost.iterations + 2
 
 
-@pytest.mark.parametrize("solver", ["bicgstab", "tfqmr"])
+# Early-iterate cases where two CPU renderings of the same iteration (A (D^-1 u) against a
+# pre-scaled A D^-1) agree to < 1e-14 at every k used: BiCGSTAB-Jacobi on the 13x7x5 cabin
+# amplifies rounding from k = 5 on (4e-14 at k = 4, 7e-4 at k = 8), so it runs on the box.
+@pytest.mark.parametrize("solver,prob,f", [
+    ("bicgstab", hi.small_box_problem(10, 8, 6), 100.0), ("tfqmr", hi.cabin_problem(13, 7, 5), 150.0)],
+    ids=["bicgstab-box", "tfqmr-cabin"])
 @pytest.mark.parametrize("k", [1, 2, 3, 8])
-def test_right_jacobi_early_iterates(solver, k):
-    prob = hi.cabin_problem(13, 7, 5)
+def test_right_jacobi_early_iterates(solver, prob, f, k):
     ctx = context(prob)
-    A, b = fem.system(prob, 150.0)
-    p, st = helm.helm_solve(ctx, [150.0], helm.make_opts(solver, tol=1e-14, maxit=k, precond="jacobi"),
+    A, b = fem.system(prob, f)
+    p, st = helm.helm_solve(ctx, [f], helm.make_opts(solver, tol=1e-14, maxit=k, precond="jacobi"),
                             raise_on_fail=False)
     mv, unscale = krylov.right_jacobi(A)
     y, ost = getattr(krylov, solver)(mv, b, tol=1e-14, maxit=k)
@@ -138,7 +144,11 @@ def test_converged_values_match_oracle(solver, precond, dims, f):
     g = p[0].cpu().numpy()
     assert st[0]["status"] == 0 and ost.converged
     assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-12
-    assert rel(g, unscale(y)) <= 1e-9
+    # BiCGSTAB / TFQMR paths drift apart with rounding, so two converged results are each within
+    # cond(A) * 1e-12 of x* rather than of each other: the GPU result must be as close to x* as
+    # the oracle's
+    xs = spl.spsolve(A.tocsc(), b)
+    assert rel(g, xs) <= max(10 * rel(unscale(y), xs), 1e-10)
 
 
 def test_jacobi_tfqmr_batch_of_sweep_lattices():
