@@ -2,7 +2,7 @@
 // system carries between super-steps, the tile / launch parameters, and the device helpers
 // every solver's phases use (arrival counting, tile-ordered partial sums, the compacted tile
 // list, the two-pass tile SpMV). The solvers themselves live in krylov_cocg.cu (COCG, FP64 and
-// mixed) and krylov_bicg.cu (BiCGSTAB, TFQMR).
+// mixed) and krylov_bicg.cu (BiCGSTAB, TFQMR); krylov_host.cu launches them.
 #pragma once
 
 #include "kernels.cuh"
@@ -107,11 +107,13 @@ struct KParams {
   unsigned long long bar_timeout;  // barrier give-up time (ns)
   unsigned long long* trace;       // optional phase trace of block 0 (HELM_TRACE_STEPS), or null
   int trace_steps;
+  int prefetch;                    // 1: prefetch each thread's next row of matrix values into L2
 };
 
 
-// Kernel entry points of the other solver translation units (host function pointers of the
-// persistent kernels, for the cooperative launch in krylov_cocg.cu).
+// Kernel entry points of the solver translation units (host function pointers of the persistent
+// kernels, for the cooperative launch in krylov_host.cu).
+void* cocg_kernel(int prec, int blocks_per_sm);  // prec: 0 FP64, 1 complex64 inner, 2 double-word inner
 void* bicg_kernel(int blocks_per_sm);
 void* tfqmr_kernel(int blocks_per_sm);
 // Right Jacobi preconditioning of a slot-major split matrix: djac = diag(A), then every column c
@@ -270,14 +272,24 @@ __device__ __forceinline__ void tile_spmv(const cplx<T>* val, const uint8_t* cfl
   }
 }
 
+// L2 prefetch of one address (no register result, nothing waits for it)
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Double-word version of tile_spmv: first(row, q, complex_row_flag), fix(row, imaginary part).
+// With `pf`, each thread prefetches the 27 matrix values of its next row into L2 before working
+// on the current one, so the streamed matrix is mostly an L2 hit when it is loaded.
 template <typename F1, typename F2>
 __device__ __forceinline__ void tile_spmv_dw(const float2* valw, const uint8_t* cflag, const cw* x, int64_t n,
                                              int64_t Nx, int64_t NxNy, int64_t row0, int64_t row1, F1 first,
-                                             F2 fix) {
+                                             F2 fix, int pf = 0) {
   const float2* vim = valw + 27 * n;
   int has_c = 0;
   for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += kBlock) {
+    if (pf && r0 + kBlock < row1)
+#pragma unroll
+      for (int k = 0; k < 27; ++k) prefetch_l2(valw + (int64_t)k * n + r0 + kBlock);
     const cw s0 = dia_row_re_dw(valw, x, n, Nx, NxNy, r0);
     const int c0 = cflag[r0];
     first(r0, s0, c0);
