@@ -14,11 +14,24 @@ clamped to the lattice (the 27-point graph distance). Artificial boundaries are
 homogeneous Dirichlet (A_s is the plain principal submatrix). Local solves are exact
 (scipy splu).
 
+Optimized Schwarz variant (``robin``; paper Sec. 4 names an optimized Schwarz method with
+absorbing, Robin-type transmission conditions on the subdomain interfaces but gives no
+parameters): A_s = R_s A R_s^T + robin * M_G,s, where M_G,s is the face mass (int Ni Nj dS, the
+same Q1 face integral as the admittance term) of every face of the extended box that lies inside
+the lattice (an artificial interface), restricted to nodes that are not Dirichlet nodes. Reading
+of the coefficient: robin = i k, the matched impedance (beta rho c = 1) of the wall term
++ i k rho c B(beta) of the operator, i.e. the first-order absorbing (Despres) condition, the same
+on both sides of an interface.
+
 Pinned (tests/test_oracle_ras.py): a 1x1x1 partition is the exact inverse (GMRES converges
-in one step); with any partition the preconditioned solution equals the direct solution.
+in one step); with any partition the preconditioned solution equals the direct solution; the
+interface mass of a box equals the scatter of fem.quad_mass over the box's interface quads.
 """
 import numpy as np
+import scipy.sparse as sp
 import scipy.sparse.linalg as spl
+
+from . import fem
 
 
 def block_ranges(npts, parts):
@@ -48,16 +61,50 @@ def _box_ids(mesh, box):
     return np.sort(ids.ravel())
 
 
+def interface_mass(mesh, ext):
+    """Face mass (n x n real CSR) of the faces of box ``ext`` that lie inside the lattice: the
+    scatter of fem.quad_mass over every quad of those faces."""
+    dims = (mesh.nx + 1, mesh.ny + 1, mesh.nz + 1)
+    h = (mesh.Lx / mesh.nx, mesh.Ly / mesh.ny, mesh.Lz / mesh.nz)
+    rows, cols, vals = [], [], []
+    for a in range(3):
+        (lo, hi) = ext[a]
+        planes = [p for p, inside in ((lo, lo > 0), (hi - 1, hi < dims[a])) if inside]
+        u, v = [b for b in range(3) if b != a]
+        Bq = fem.quad_mass(h[u], h[v])
+        for pa in sorted(set(planes)):
+            for cu in range(ext[u][0], ext[u][1] - 1):
+                for cv in range(ext[v][0], ext[v][1] - 1):
+                    ids = []
+                    for b2 in (0, 1):
+                        for b1 in (0, 1):
+                            idx = [0, 0, 0]
+                            idx[a], idx[u], idx[v] = pa, cu + b1, cv + b2
+                            ids.append(idx[0] + dims[0] * (idx[1] + dims[1] * idx[2]))
+                    for r in range(4):
+                        for c in range(4):
+                            rows.append(ids[r]); cols.append(ids[c]); vals.append(Bq[r, c])
+    n = dims[0] * dims[1] * dims[2]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
 class RAS:
-    def __init__(self, A, mesh, parts=(8, 4, 4), overlap=2):
+    def __init__(self, A, mesh, parts=(8, 4, 4), overlap=2, robin=None, dir_nodes=None):
         A = A.tocsr()
         self.n = A.shape[0]
         self.blocks = []
+        free = np.ones(self.n, dtype=bool)
+        if dir_nodes is not None:
+            free[np.asarray(dir_nodes)] = False
         for own, ext in subdomains(mesh, parts, overlap):
             E = _box_ids(mesh, ext)
             O = _box_ids(mesh, own)
             keep = np.searchsorted(E, O)  # positions of owned nodes inside E
-            lu = spl.splu(A[E][:, E].tocsc())
+            As = A[E][:, E]
+            if robin is not None:
+                F = sp.diags(free[E].astype(np.float64))
+                As = As + robin * (F @ interface_mass(mesh, ext)[E][:, E] @ F)
+            lu = spl.splu(As.tocsc())
             self.blocks.append((E, O, keep, lu))
 
     def __call__(self, r):
