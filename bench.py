@@ -560,13 +560,18 @@ def run_configs(args):
         o2 = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
         _, st2, dt2, pr2 = run(c, [f], o2)
         _, st3, dt3, _ = run(c, [f], helm.make_opts("bicgstab", tol=TOL, maxit=40000))
+        o4 = helm.make_opts("gmres", restart=50, tol=TOL, maxit=5000, precond="oras", ras_parts=(8, 4, 4), ras_overlap=2)
+        _, st4, dt4, pr4 = run(c, [f], o4)
         out["%g" % f] = {"ras_gmres50": {"ms_total": dt * 1e3, "solve_ms": pr_["solve_ms"],
                                          "iterations": st[0]["iterations"], "relres": st[0]["relres"],
                                          "status": st[0]["status"]},
                          "cocg": {"ms_total": dt2 * 1e3, "iterations": st2[0]["iterations"],
                                   "relres": st2[0]["relres"], "status": st2[0]["status"]},
                          "bicgstab": {"ms_total": dt3 * 1e3, "iterations": st3[0]["iterations"],
-                                      "relres": st3[0]["relres"], "status": st3[0]["status"]}}
+                                      "relres": st3[0]["relres"], "status": st3[0]["status"]},
+                         "oras_gmres50": {"ms_total": dt4 * 1e3, "solve_ms": pr4["solve_ms"],
+                                          "iterations": st4[0]["iterations"], "relres": st4[0]["relres"],
+                                          "status": st4[0]["status"]}}
     res["cabin282k"] = out
     # cabin2m: every 8th of the 32 frequencies, FP64 vs mixed, batched per precision
     pr = hi.cabin_problem(200, 112, 96)
@@ -574,6 +579,8 @@ def run_configs(args):
     fr = list(np.geomspace(100.0, 400.0, 32)[::8])
     p64, st64, dt64, _ = run(c, fr, helm.make_opts("cocg", tol=TOL, maxit=60000, stall_window=STALL))
     pmx, stmx, dtmx, _ = run(c, fr, mixed_opts(helm, 60000))
+    pdw, stdw, dtdw, _ = run(c, fr, dw_opts(helm, 60000, "jacobi"))
+    err_dw = [float((torch.linalg.norm(pdw[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
     err = [float((torch.linalg.norm(pmx[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
     res["cabin2m_sample"] = {"freqs": [float(f) for f in fr], "n": c.n,
                              "fp64": {"freqs_per_s": len(fr) / dt64, "iterations": [s_["iterations"] for s_ in st64],
@@ -581,8 +588,10 @@ def run_configs(args):
                              "mixed": {"freqs_per_s": len(fr) / dtmx, "iterations": [s_["iterations"] for s_ in stmx],
                                        "c64": [s_["iterations_c64"] for s_ in stmx], "outer": [s_["outer"] for s_ in stmx],
                                        "status": [s_["status"] for s_ in stmx]},
-                             "rel_l2_mixed_vs_fp64": err}
-    del p64, pmx
+                             "rel_l2_mixed_vs_fp64": err,
+                             "dw_jacobi": {"freqs_per_s": len(fr) / dtdw, "iterations": [s_["iterations"] for s_ in stdw],
+                                           "status": [s_["status"] for s_ in stdw], "rel_l2_vs_fp64": err_dw}}
+    del p64, pmx, pdw
     # adjoint64: 64 frequencies 20-300 Hz on the 282k cabin, forward + adjoint
     pr = hi.cabin_problem(100, 56, 48)
     c = ctx_of(pr)
@@ -607,7 +616,8 @@ def run_configs(args):
     amp = torch.from_numpy(hi.resonance_spectrum(np.array(fr))).cuda()
     w = torch.from_numpy(hi.listener_weights(pr.mesh)).cuda()
     out = {"n": c.n, "freqs": [fr[0], fr[-1], len(fr)]}
-    for name, o in (("fp64", fp64_opts(helm, 40000)), ("dw", dw_opts(helm, 40000))):
+    for name, o in (("fp64", fp64_opts(helm, 40000)), ("dw", dw_opts(helm, 40000)),
+                    ("dw_jacobi", dw_opts(helm, 40000, "jacobi"))):
         run(c, fr, o)
         p, st, dt, _ = run(c, fr, o)
         level = [float((abs(amp[k]) ** 2 * (w * (p[k].abs() ** 2)).sum()).item()) for k in range(len(fr))]

@@ -63,7 +63,8 @@ typedef enum {
 enum { HELM_C128 = 0, HELM_C64 = 1 };                 /* matrix value precision */
 enum { HELM_FMT_CSR = 0, HELM_FMT_DIA27 = 1 };         /* matrix layout (see helm_assemble) */
 enum { HELM_SOLVER_GMRES = 0, HELM_SOLVER_COCG = 1, HELM_SOLVER_BICGSTAB = 2, HELM_SOLVER_TFQMR = 3 }; /* Krylov method */
-enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1, HELM_PRECOND_JACOBI = 2 }; /* right preconditioner */
+enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1, HELM_PRECOND_JACOBI = 2, HELM_PRECOND_ORAS = 3 };
+/* preconditioner (right, except the symmetric Jacobi form of COCG) */
 
 typedef struct {
   int32_t solver;       /* HELM_SOLVER_GMRES: restarted GMRES(restart), CGS2 Arnoldi, complex
@@ -75,7 +76,12 @@ typedef struct {
   int32_t restart;      /* GMRES cycle length m (1..128) */
   double tol;           /* stop when the true ||b - A p||_2 / ||b||_2 <= tol */
   int32_t maxit;        /* Krylov steps (SpMVs inside the iteration) before HELM_NOT_CONVERGED */
-  int32_t precond;      /* HELM_PRECOND_NONE; HELM_PRECOND_RAS (GMRES only); HELM_PRECOND_JACOBI
+  int32_t precond;      /* HELM_PRECOND_NONE; HELM_PRECOND_RAS (GMRES only); HELM_PRECOND_ORAS (GMRES
+                           only): RAS whose subdomain matrices carry the optimized-Schwarz interface
+                           term i k M_G (face mass of the subdomain's faces inside the lattice,
+                           Dirichlet nodes excluded; paper Sec. 4 names absorbing Robin interface
+                           conditions, i k is the matched impedance of the wall term);
+                           HELM_PRECOND_JACOBI
                            (not GMRES), the reading of the paper's unnamed "P": BiCGSTAB / TFQMR
                            run on A D^-1 (D = diag(A), right Jacobi) and return x = D^-1 y; COCG
                            (FP64 or mixed) runs on S A S with S = D^-1/2 (principal root; stays

@@ -53,10 +53,11 @@ bool valid_opts(const helm_solve_opts* o) {
     return false;
   if (!(o->tol > 0.0) || o->maxit < 1) return false;
   if (o->solver == HELM_SOLVER_GMRES && (o->restart < 1 || o->restart > 128)) return false;
-  if (o->precond != HELM_PRECOND_NONE && o->precond != HELM_PRECOND_RAS && o->precond != HELM_PRECOND_JACOBI)
+  if (o->precond != HELM_PRECOND_NONE && o->precond != HELM_PRECOND_RAS && o->precond != HELM_PRECOND_JACOBI &&
+      o->precond != HELM_PRECOND_ORAS)
     return false;
   if (o->precond == HELM_PRECOND_JACOBI && o->solver == HELM_SOLVER_GMRES) return false;
-  if (o->precond == HELM_PRECOND_RAS) {
+  if (o->precond == HELM_PRECOND_RAS || o->precond == HELM_PRECOND_ORAS) {
     if (o->solver != HELM_SOLVER_GMRES) return false;
     if (o->ras_parts[0] < 1 || o->ras_parts[1] < 1 || o->ras_parts[2] < 1 || o->ras_overlap < 0) return false;
   }

@@ -405,7 +405,7 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   const size_t nV = (size_t)(m + 1) * n;
   cd* ws = nullptr;
   const size_t ncd = 3 * (size_t)n /*r,w,u*/ + nV + (size_t)(m + 1) * m + 3 * (m + 1) + 2 * m +
-                     (size_t)ntiles * (m + 1) + (o.precond == HELM_PRECOND_RAS ? n : 0);
+                     (size_t)ntiles * (m + 1) + (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS ? n : 0);
   helm_status stt = dev_alloc(&ws, ncd + 2 * m /*cs*/ + 8);
   if (stt != HELM_OK) return stt;
   GmCtl* dctl = nullptr;
@@ -438,7 +438,7 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   a.y = p; p += m;
   a.part = p; p += (size_t)ntiles * (m + 1);
   a.z = nullptr;
-  if (o.precond == HELM_PRECOND_RAS) { a.z = p; p += n; }
+  if (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS) { a.z = p; p += n; }
   a.cs = reinterpret_cast<double*>(p);
   a.ctl = dctl;
   a.tol = o.tol;
@@ -451,8 +451,11 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   GmCtl* hctl = nullptr;
   cudaError_t e = cudaMallocHost((void**)&hctl, sizeof(GmCtl));
   if (e != cudaSuccess) result = cuda_error(e, "cudaMallocHost");
-  if (result == HELM_OK && o.precond == HELM_PRECOND_RAS) {
-    result = ras_create(ctx, rowptr, col, val, o.ras_parts, o.ras_overlap, &ras, s);
+  if (result == HELM_OK && (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS)) {
+    // optimized Schwarz: Robin coefficient i k, the matched impedance of the wall term
+    const double k = 2.0 * 3.14159265358979323846 * freq / ctx->phys.c;
+    const cd robin = o.precond == HELM_PRECOND_ORAS ? cd(0.0, k) : cd(0.0, 0.0);
+    result = ras_create(ctx, rowptr, col, val, o.ras_parts, o.ras_overlap, robin, &ras, s);
   }
   if (result == HELM_OK) {
     e = cudaMemsetAsync(dctl, 0, sizeof(GmCtl), s);

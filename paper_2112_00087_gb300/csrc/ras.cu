@@ -89,6 +89,52 @@ __global__ void ras_extract(const RasSub* __restrict__ subs, const int32_t* __re
   }
 }
 
+// Optimized-Schwarz interface term: robin * (face mass of the extended box's faces that lie
+// inside the lattice), added to the lower band by columns, Dirichlet rows and columns excluded.
+// On a face plane with in-plane axes u, v the Q1 face mass is M1_u (x) M1_v, M1 the 1D linear
+// mass over the face's extent: diagonal h/3 per adjacent interval, neighbours h/6. Thread k owns
+// column k of the band, so no two threads write the same entry.
+__device__ __forceinline__ double mass1d(int c, int dc, int lo, int hi, double h) {
+  if (dc == 0) return (h / 3.0) * ((c > lo ? 1 : 0) + (c < hi - 1 ? 1 : 0));
+  const int c2 = c + dc;
+  return (c2 >= lo && c2 < hi) ? h / 6.0 : 0.0;
+}
+
+__global__ void ras_robin(const RasSub* __restrict__ subs, const uint8_t* __restrict__ is_dir, cd* __restrict__ W,
+                          int Nx, int Ny, int Nz, double hx, double hy, double hz, cd robin) {
+  const RasSub S = subs[blockIdx.x];
+  cd* Ws = W + S.off;
+  const int N[3] = {Nx, Ny, Nz};
+  const int lo[3] = {S.i0, S.j0, S.l0};
+  const double h[3] = {hx, hy, hz};
+  for (int k = threadIdx.x; k < S.ns; k += blockDim.x) {
+    int p[3];
+    local_to_lattice(S, k, p[0], p[1], p[2]);
+    if (is_dir[p[0] + (int64_t)Nx * (p[1] + (int64_t)Ny * p[2])]) continue;
+    for (int a = 0; a < 3; ++a) {
+      const int hi_a = lo[a] + S.e[a];
+      const bool on_lo = p[a] == lo[a] && lo[a] > 0;
+      const bool on_hi = p[a] == hi_a - 1 && hi_a < N[a];
+      if (!on_lo && !on_hi) continue;  // (a one-layer box counts its single plane once)
+      const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
+      for (int du = -1; du <= 1; ++du)
+        for (int dv = -1; dv <= 1; ++dv) {
+          const double m = mass1d(p[u], du, lo[u], lo[u] + S.e[u], h[u]) * mass1d(p[v], dv, lo[v], lo[v] + S.e[v], h[v]);
+          if (m == 0.0) continue;
+          int q[3] = {p[0], p[1], p[2]};
+          q[u] += du;
+          q[v] += dv;
+          if (is_dir[q[0] + (int64_t)Nx * (q[1] + (int64_t)Ny * q[2])]) continue;
+          const int kc = lattice_to_local(S, q[0], q[1], q[2]);
+          if (kc < k) continue;  // the upper part of column k is the transpose, not stored
+          const int d = kc - k;
+          cd& w = Ws[(int64_t)k * (S.bw + 1) + d];
+          w = cd(w.re + m * robin.re, w.im + m * robin.im);
+        }
+    }
+  }
+}
+
 // Right-looking band LDL^T, one CTA per subdomain. After column k: W[k][0] = D_k,
 // W[k][d] = L(k+d, k).
 __global__ void ras_factor(const RasSub* __restrict__ subs, cd* __restrict__ W, int* __restrict__ status) {
@@ -218,7 +264,7 @@ std::vector<std::pair<int, int>> block_ranges(int npts, int parts) {
 }  // namespace
 
 helm_status ras_create(const helm_ctx* ctx, const int32_t* rowptr, const int32_t* col, const cd* val,
-                       const int32_t parts[3], int overlap, RasPrecond** out, cudaStream_t s) {
+                       const int32_t parts[3], int overlap, cd robin, RasPrecond** out, cudaStream_t s) {
   *out = nullptr;
   const int N[3] = {ctx->mesh.nx + 1, ctx->mesh.ny + 1, ctx->mesh.nz + 1};
   for (int a = 0; a < 3; ++a)
@@ -283,6 +329,10 @@ helm_status ras_create(const helm_ctx* ctx, const int32_t* rowptr, const int32_t
     e = cudaFuncSetAttribute(ras_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     ras_extract<<<P->nsub, 256, 0, s>>>(P->d_sub, rowptr, col, val, P->colband, P->Nx, P->Ny);
+    if (robin.re != 0.0 || robin.im != 0.0)
+      ras_robin<<<P->nsub, 256, 0, s>>>(P->d_sub, ctx->is_dir, P->colband, N[0], N[1], N[2],
+                                        ctx->mesh.Lx / ctx->mesh.nx, ctx->mesh.Ly / ctx->mesh.ny,
+                                        ctx->mesh.Lz / ctx->mesh.nz, robin);
     ras_factor<<<P->nsub, 512, 0, s>>>(P->d_sub, P->colband, P->d_status);
     ras_transpose<<<P->nsub, 256, 0, s>>>(P->d_sub, P->colband, P->rowband);
     e = cudaGetLastError();

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "NOT_CONV
 HELM_C128, HELM_C64 = 0, 1
 HELM_FMT_CSR, HELM_FMT_DIA27 = 0, 1
 HELM_SOLVER_GMRES, HELM_SOLVER_COCG, HELM_SOLVER_BICGSTAB, HELM_SOLVER_TFQMR = 0, 1, 2, 3
-HELM_PRECOND_NONE, HELM_PRECOND_RAS, HELM_PRECOND_JACOBI = 0, 1, 2
+HELM_PRECOND_NONE, HELM_PRECOND_RAS, HELM_PRECOND_JACOBI, HELM_PRECOND_ORAS = 0, 1, 2, 3
 
 # Symbols declared in include/helm.h (tests check the library exports all of them).
 EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary", "helm_sizes",
@@ -138,7 +138,8 @@ def make_opts(solver="cocg", restart=50, tol=1e-10, maxit=100000, precond=None, 
     o.restart = restart
     o.tol = tol
     o.maxit = maxit
-    o.precond = {None: HELM_PRECOND_NONE, "ras": HELM_PRECOND_RAS, "jacobi": HELM_PRECOND_JACOBI}[precond]
+    o.precond = {None: HELM_PRECOND_NONE, "ras": HELM_PRECOND_RAS, "jacobi": HELM_PRECOND_JACOBI,
+                 "oras": HELM_PRECOND_ORAS}[precond]
     o.ras_parts[:] = list(ras_parts)
     o.ras_overlap = ras_overlap
     # mixed: False / True (complex64 inner) / "c64" / "dw" (double-word inner)

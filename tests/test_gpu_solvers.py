@@ -143,6 +143,28 @@ def test_gmres_ras_matches_oracle(dims, parts, f):
         assert st[0]["iterations"] == 1
 
 
+@pytest.mark.parametrize("dims,parts,overlap,f", [((12, 10, 8), (3, 2, 2), 1, 200.0), ((25, 14, 12), (4, 2, 2), 2, 100.0),
+                                                  ((25, 14, 12), (4, 2, 2), 0, 100.0), ((6, 5, 4), (1, 1, 1), 2, 150.0)])
+def test_gmres_optimized_schwarz_matches_oracle(dims, parts, overlap, f):
+    # Robin interface term i k M_G on every subdomain's artificial faces (paper Sec. 4 optimized
+    # Schwarz; coefficient reading i k), against the oracle's construction of the same matrices
+    prob = hi.cabin_problem(*dims) if dims[0] > 20 else hi.small_box_problem(*dims)
+    ctx = context(prob)
+    o = helm.make_opts("gmres", restart=50, tol=1e-10, maxit=5000, precond="oras", ras_parts=parts,
+                       ras_overlap=overlap)
+    p, st = helm.helm_solve(ctx, [f], o)
+    A, b = fem.system(prob, f)
+    k = 2 * np.pi * f / prob.c
+    P = ras.RAS(A, prob.mesh, parts=parts, overlap=overlap, robin=1j * k, dir_nodes=prob.dir_nodes)
+    x, ost = krylov.gmres(lambda v: A @ v, b, 50, tol=1e-10, maxit=5000, precond=P)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0 and ost.converged
+    assert within5(st[0]["iterations"], ost.iterations), (st[0], ost.iterations)
+    assert rel(g, x) <= 1e-9
+    if parts == (1, 1, 1):
+        assert st[0]["iterations"] == 1
+
+
 @pytest.mark.parametrize("dims,f", [((20, 16, 12), 100.0), ((40, 22, 19), 150.0)])
 def test_mixed_precision_refinement(dims, f):
     prob = hi.small_box_problem(*dims) if dims[0] == 20 else hi.cabin_problem(*dims)
