@@ -651,11 +651,12 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
   dacc rr_, ri_;
   float nrm = 0.f;  // ||r||^2 for the stopping estimate (FP32 is enough for a threshold test)
   for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-    if (P.prefetch && i + kBlock < T.row1) {
-      prefetch_l2(Y.pw + i + kBlock);
-      prefetch_l2(Y.qw + i + kBlock);
-      prefetch_l2(Y.xw + i + kBlock);
-      prefetch_l2(Y.rw + i + kBlock);
+    const int64_t ia = i + (int64_t)P.prefetch * kBlock;
+    if (P.prefetch && ia < T.row1) {
+      prefetch_l2(Y.pw + ia);
+      prefetch_l2(Y.qw + ia);
+      prefetch_l2(Y.xw + ia);
+      prefetch_l2(Y.rw + ia);
     }
     const cw pv = Y.pw[i], qv = Y.qw[i];
     const cw xn = cw_axpy(Y.xw[i], a, pv);

@@ -107,7 +107,7 @@ struct KParams {
   unsigned long long bar_timeout;  // barrier give-up time (ns)
   unsigned long long* trace;       // optional phase trace of block 0 (HELM_TRACE_STEPS), or null
   int trace_steps;
-  int prefetch;                    // 1: prefetch each thread's next row of matrix values into L2
+  int prefetch;                    // d > 0: prefetch each thread's row d rows-of-the-block ahead into L2
 };
 
 
@@ -278,18 +278,20 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 
 // Double-word version of tile_spmv: first(row, q, complex_row_flag), fix(row, imaginary part).
-// With `pf`, each thread prefetches the 27 matrix values of its next row into L2 before working
-// on the current one, so the streamed matrix is mostly an L2 hit when it is loaded.
+// With `pf` = d > 0, each thread prefetches the 27 matrix values of the row it will reach d
+// iterations later into L2 before working on the current one, so the streamed matrix is mostly
+// an L2 hit when it is loaded.
 template <typename F1, typename F2>
 __device__ __forceinline__ void tile_spmv_dw(const float2* valw, const uint8_t* cflag, const cw* x, int64_t n,
                                              int64_t Nx, int64_t NxNy, int64_t row0, int64_t row1, F1 first,
                                              F2 fix, int pf = 0) {
   const float2* vim = valw + 27 * n;
   int has_c = 0;
+  const int64_t ahead = (int64_t)pf * kBlock;
   for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += kBlock) {
-    if (pf && r0 + kBlock < row1)
+    if (pf && r0 + ahead < row1)
 #pragma unroll
-      for (int k = 0; k < 27; ++k) prefetch_l2(valw + (int64_t)k * n + r0 + kBlock);
+      for (int k = 0; k < 27; ++k) prefetch_l2(valw + (int64_t)k * n + r0 + ahead);
     const cw s0 = dia_row_re_dw(valw, x, n, Nx, NxNy, r0);
     const int c0 = cflag[r0];
     first(r0, s0, c0);

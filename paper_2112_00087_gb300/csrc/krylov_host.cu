@@ -215,8 +215,8 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   P.stall = o.stall_window;
   P.trace = d_trace;
   P.trace_steps = trace_steps;
-  const char* pfenv = getenv("HELM_PREFETCH");  // tuning knob: 0 disables the L2 prefetch
-  P.prefetch = pfenv ? (atoi(pfenv) != 0) : 1;
+  const char* pfenv = getenv("HELM_PREFETCH");  // tuning knob: prefetch distance in block rows, 0 = off
+  P.prefetch = pfenv ? std::max(0, std::min(atoi(pfenv), 8)) : 1;
   // Host-side fault injection for tests (never set in normal use): the barriers wait for one
   // block that does not exist and give up after 200 ms, so the launch ends with HELM_TIMEOUT
   // without faulting or hanging the GPU.
