@@ -335,6 +335,63 @@ def spmv_roofline(helm, torch, peak_gbs):
     return out
 
 
+def spmm_multi_roofline(helm, torch, peak_gbs, nfreqs=(8, 32)):
+    """Shared-mesh multi-frequency product on the 2,203,161-node lattice against one DIA-27 product
+    per frequency (matrices pre-assembled), complex128 and complex64, L2 flushed between reps."""
+    pr = hi.cabin_problem(200, 112, 96)
+    m = pr.mesh
+    ctx = helm.Context(m.nx, m.ny, m.nz, m.Lx, m.Ly, m.Lz)
+    ctx.set_boundary(torch.from_numpy(pr.beta).cuda(), torch.from_numpy(pr.dir_nodes).cuda(),
+                     torch.from_numpy(pr.p_dir).cuda())
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    n = ctx.n
+
+    def timed_med(fn, reps=7):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1000.0)
+        return statistics.median(ts)
+
+    out = {}
+    for prec, dt, vb, name in ((helm.HELM_C128, torch.complex128, 16, "c128"), (helm.HELM_C64, torch.complex64, 8, "c64")):
+        S = helm.helm_assemble_shared(ctx, prec)
+        for F in nfreqs:
+            freqs = list(np.geomspace(100.0, 400.0, F))
+            X = torch.randn(F, n, dtype=dt, device="cuda")
+            Y = torch.empty_like(X)
+            t_multi = timed_med(lambda: helm.helm_spmv_multi(S, freqs, X, Y))
+            # one pre-assembled DIA-27 matrix per frequency (at most 8 resident: reuse them cyclically)
+            mats = [helm.helm_assemble(ctx, f, prec, with_rhs=False, fmt=helm.HELM_FMT_DIA27) for f in freqs[:8]]
+
+            def single():
+                for f in range(F):
+                    helm.helm_spmv(mats[f % len(mats)], X[f], Y[f])
+            t_single = timed_med(single, reps=3)
+            for A in mats:
+                A.free()
+            passes = (F + 7) // 8
+            b_multi = passes * (27 * n * vb + n) + F * 2 * vb * n
+            b_single = F * dia_spmv_bytes(n, vb)
+            out["%s_F%d" % (name, F)] = {
+                "multi_ms_per_freq": t_multi / F * 1e3, "single_ms_per_freq": t_single / F * 1e3,
+                "speedup": t_single / t_multi, "multi_gbs": b_multi / t_multi / 1e9,
+                "multi_frac": b_multi / t_multi / 1e9 / peak_gbs, "single_gbs": b_single / t_single / 1e9,
+                "bytes_per_freq_multi": b_multi / F, "bytes_per_freq_single": b_single / F}
+            del X, Y
+        S.close()
+    ctx.close()
+    return out
+
+
 def cpu_oracle_sample(budget_s=20.0, nfreq=256):
     """The CPU oracle (numpy/scipy COCG) on every 16th frequency of the sweep, ascending, until
     the time budget is spent. Returns (freqs done, seconds, cores, description)."""
@@ -625,6 +682,8 @@ def run_configs(args):
                      "converged": sum(1 for s_ in st if s_["status"] == 0),
                      "listener_peak_hz": fr[int(np.argmax(level))]}
     res["resonance64"] = out
+    peaks, _ = measured_peaks()
+    res["spmm_cabin2m"] = spmm_multi_roofline(helm, torch, float(peaks["hbm_gbs"]))
     print(json.dumps({"configs": res}), flush=True)
 
 

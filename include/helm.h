@@ -135,6 +135,7 @@ typedef struct {
 
 typedef struct helm_ctx helm_ctx;       /* one lattice + physics + boundary data */
 typedef struct helm_matrix helm_matrix; /* one assembled, eliminated system matrix (CSR) */
+typedef struct helm_shared helm_shared; /* frequency-independent parts K, M, B of a lattice */
 
 /* Last error message of the calling thread ("" if none). Owned by the library. */
 const char* helm_last_error(void);
@@ -189,6 +190,25 @@ helm_status helm_matrix_dia27(const helm_matrix* A, int64_t* n, int32_t* precisi
  * complex [n] in the matrix precision (complex64 matrices accumulate in FP32), must not overlap. Ordered on
  * `stream` (cudaStream_t; NULL = the context stream of the matrix). */
 helm_status helm_spmv(const helm_matrix* A, const void* x, void* y, void* stream);
+
+/* Frequency-independent parts of the context's eliminated operator A(k) = K - k^2 M
+ * + i k rho c B(beta) (paper Sec. 3.2): K, M and the wall term B, slot-major like DIA27, with the
+ * Dirichlet rows of K set to the identity and Dirichlet rows / columns of M, B and the other K
+ * entries zero, so that A(k) of every frequency is the eliminated system matrix of helm_assemble
+ * (the k-dependent lifting of b is not part of the operator). precision: HELM_C128 (FP64 parts)
+ * or HELM_C64 (FP32 copies as well). Needs helm_set_boundary first; reflects the boundary data at
+ * the time of the call. *out is owned by the caller until helm_shared_free; the context must
+ * outlive it. Ordered on the context stream. */
+helm_status helm_assemble_shared(helm_ctx* ctx, int32_t precision, helm_shared** out);
+void helm_shared_free(helm_shared* S);
+
+/* Shared-mesh multi-frequency product ("SpMM"): Y[f] = A(2 pi freqs_hz[f] / c) X[f] for
+ * f < nfreq, reading K and M once per row for up to 8 frequencies at a time (B only on rows with
+ * a wall term). X, Y (dev) complex in the precision of S, frequency-major [nfreq][n], must not
+ * overlap; freqs_hz (host) >= 0. No counterpart in the paper's code: its FRF evaluates the
+ * operator one frequency at a time. Ordered on `stream` (NULL = the context stream). */
+helm_status helm_spmv_multi(const helm_shared* S, const double* freqs_hz, int32_t nfreq, const void* X,
+                            void* Y, void* stream);
 
 /* Reductions over complex128 vectors x, y (dev, [n]), FP64 accumulation in a fixed order:
  * op 0: x^H y (conjugated, GMRES), op 1: x^T y (unconjugated, COCG), op 2: ||x||_2 (y unused).

@@ -199,6 +199,78 @@ helm_status assemble_values(const helm_ctx* ctx, double freq, cd* val, cd* b, cu
   return HELM_OK;
 }
 
+// Frequency-independent parts of the eliminated matrix, slot-major like the DIA-27 values:
+// comp = [K | M | Re B | Im B], each 27 n doubles, with A(k) = K - k^2 M + i k rho c B on free
+// rows and columns; a Dirichlet row holds K = 1 on the diagonal and zeros elsewhere, a Dirichlet
+// column zeros (the lifting term, which depends on k, is not part of the operator). bflag[r] = 1
+// for rows with a non-zero B entry.
+__global__ void components_kernel(Lattice L, const cd* __restrict__ beta, const uint8_t* __restrict__ is_dir,
+                                  double* __restrict__ comp, uint8_t* __restrict__ bflag, int64_t n) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int i = (int)(r % L.Nx);
+  int j = (int)((r / L.Nx) % L.Ny);
+  int l = (int)(r / ((int64_t)L.Nx * L.Ny));
+  const int64_t o_xm = 0, o_xp = (int64_t)L.ny * L.nz, o_ym = 2 * o_xp,
+                o_yp = o_ym + (int64_t)L.nx * L.nz, o_zm = o_yp + (int64_t)L.nx * L.nz,
+                o_zp = o_zm + (int64_t)L.nx * L.ny;
+  const bool rowD = is_dir != nullptr && is_dir[r] != 0;
+  double* Kc = comp;
+  double* Mc = comp + 27 * n;
+  double* Br = comp + 54 * n;
+  double* Bi = comp + 81 * n;
+  for (int s = 0; s < 27; ++s) {
+    Kc[(int64_t)s * n + r] = 0.0;
+    Mc[(int64_t)s * n + r] = 0.0;
+    Br[(int64_t)s * n + r] = 0.0;
+    Bi[(int64_t)s * n + r] = 0.0;
+  }
+  bool has_b = false;
+  for (int dl = -1; dl <= 1; ++dl) {
+    if (l + dl < 0 || l + dl >= L.Nz) continue;
+    double kz, mz;
+    entries1(l, dl, L.nz, L.hz, kz, mz);
+    for (int dj = -1; dj <= 1; ++dj) {
+      if (j + dj < 0 || j + dj >= L.Ny) continue;
+      double ky, my;
+      entries1(j, dj, L.ny, L.hy, ky, my);
+      for (int di = -1; di <= 1; ++di) {
+        if (i + di < 0 || i + di >= L.Nx) continue;
+        const int64_t e = (int64_t)((di + 1) + 3 * (dj + 1) + 9 * (dl + 1)) * n + r;
+        double kx, mx;
+        entries1(i, di, L.nx, L.hx, kx, mx);
+        const int64_t c = r + di + (int64_t)L.Nx * (dj + (int64_t)L.Ny * dl);
+        if (rowD) {
+          Kc[e] = c == r ? 1.0 : 0.0;
+          continue;
+        }
+        if (is_dir != nullptr && is_dir[c]) continue;
+        Kc[e] = kx * my * mz + mx * ky * mz + mx * my * kz;
+        Mc[e] = mx * my * mz;
+        cd B(0.0, 0.0);
+        if (beta != nullptr) {
+          if (di == 0 && i == 0) side_term(beta, o_xm, j, dj, L.ny, L.hy, l, dl, L.nz, L.hz, B);
+          if (di == 0 && i == L.nx) side_term(beta, o_xp, j, dj, L.ny, L.hy, l, dl, L.nz, L.hz, B);
+          if (dj == 0 && j == 0) side_term(beta, o_ym, i, di, L.nx, L.hx, l, dl, L.nz, L.hz, B);
+          if (dj == 0 && j == L.ny) side_term(beta, o_yp, i, di, L.nx, L.hx, l, dl, L.nz, L.hz, B);
+          if (dl == 0 && l == 0) side_term(beta, o_zm, i, di, L.nx, L.hx, j, dj, L.ny, L.hy, B);
+          if (dl == 0 && l == L.nz) side_term(beta, o_zp, i, di, L.nx, L.hx, j, dj, L.ny, L.hy, B);
+        }
+        Br[e] = B.re;
+        Bi[e] = B.im;
+        has_b |= (B.re != 0.0 || B.im != 0.0);
+      }
+    }
+  }
+  bflag[r] = has_b ? 1 : 0;
+}
+
+__global__ void cast_real_kernel(const double* __restrict__ v, float* __restrict__ v32, int64_t m) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; t < m; t += stride) v32[t] = __double2float_rn(v[t]);
+}
+
 // Double-word copy of m doubles: out[t] = (hi, lo), hi = fl32(v), lo = fl32(v - hi).
 __global__ void split_kernel(const double* __restrict__ v, float2* __restrict__ out, int64_t m) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -208,6 +280,18 @@ __global__ void split_kernel(const double* __restrict__ v, float2* __restrict__ 
     const float hi = __double2float_rn(a);
     out[t] = make_float2(hi, __double2float_rn(a - (double)hi));
   }
+}
+
+helm_status assemble_components(const helm_ctx* ctx, double* comp, float* comp32, uint8_t* bflag, cudaStream_t s) {
+  Lattice L = make_lattice(ctx->mesh);
+  const unsigned blocks = (unsigned)((ctx->n + 127) / 128);
+  components_kernel<<<blocks, 128, 0, s>>>(L, ctx->beta, ctx->is_dir, comp, bflag, ctx->n);
+  if (comp32) {
+    const int64_t m = 108 * ctx->n;
+    cast_real_kernel<<<(unsigned)std::min<int64_t>((m + 255) / 256, 152 * 16), 256, 0, s>>>(comp, comp32, m);
+  }
+  HELM_CUDA(cudaGetLastError());
+  return HELM_OK;
 }
 
 helm_status split_values(const double* val, float2* out, int64_t m, cudaStream_t s) {

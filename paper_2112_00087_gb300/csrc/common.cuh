@@ -105,6 +105,15 @@ struct helm_matrix {
   uint8_t* cflag;       // DIA27: 1 for rows with a non-zero imaginary entry
 };
 
+struct helm_shared {
+  const helm_ctx* ctx;  // lattice and boundary data owner (must outlive this object)
+  int64_t n;
+  int32_t precision;
+  double* comp;         // [K | M | Re B | Im B], 4 x 27 n doubles
+  float* comp32;        // the same in FP32 (HELM_C64 only)
+  uint8_t* bflag;       // [n] rows with a wall term
+};
+
 namespace helm {
 
 // assemble.cu
@@ -115,6 +124,9 @@ helm_status build_pattern(helm_ctx* ctx);
 helm_status assemble_values(const helm_ctx* ctx, double freq, cd* val, cd* b, cudaStream_t s,
                             bool eliminate = true, bool dia = false, uint8_t* cflag = nullptr);
 helm_status cast_values(const cd* val, cf* val32, int64_t nnz, cudaStream_t s);
+// frequency-independent parts [K | M | Re B | Im B] (each 27 n, slot-major) of the eliminated
+// matrix, their FP32 copy (if comp32 != null) and the rows with a wall term
+helm_status assemble_components(const helm_ctx* ctx, double* comp, float* comp32, uint8_t* bflag, cudaStream_t s);
 // double-word (hi, lo) float pairs of m doubles
 helm_status split_values(const double* val, float2* out, int64_t m, cudaStream_t s);
 

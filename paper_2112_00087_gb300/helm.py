@@ -29,7 +29,7 @@ HELM_PRECOND_NONE, HELM_PRECOND_RAS, HELM_PRECOND_JACOBI, HELM_PRECOND_ORAS = 0,
 EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary", "helm_sizes",
             "helm_assemble", "helm_matrix_free", "helm_matrix_csr", "helm_matrix_dia27", "helm_spmv", "helm_reduce",
             "helm_solve", "helm_solve_batch", "helm_adjoint_grad", "helm_adjoint_seed", "helm_last_profile",
-            "helm_reduce_noalloc"]
+            "helm_reduce_noalloc", "helm_assemble_shared", "helm_shared_free", "helm_spmv_multi"]
 
 
 class HelmError(RuntimeError):
@@ -97,6 +97,9 @@ def _load():
         "helm_adjoint_grad": (i32, [vp, P(d), i32, P(SolveOpts), vp, vp, vp, vp, P(d)]),
         "helm_adjoint_seed": (i32, [vp, P(d), i32, P(SolveOpts), vp, vp, vp, vp]),
         "helm_last_profile": (i32, [P(Profile)]),
+        "helm_assemble_shared": (i32, [vp, i32, P(vp)]),
+        "helm_shared_free": (None, [vp]),
+        "helm_spmv_multi": (i32, [vp, P(d), i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,6 +285,43 @@ def helm_spmv(A: Matrix, x: torch.Tensor, y: torch.Tensor, stream=None):
     want = torch.complex64 if A.precision == HELM_C64 else torch.complex128
     assert x.dtype == want and y.dtype == want and x.numel() == A.n and y.numel() == A.n
     _check(LIB.helm_spmv(A.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+class SharedOperator:
+    """helm_assemble_shared result: K, M, B of the context's lattice, for helm_spmv_multi."""
+
+    def __init__(self, ctx: Context, precision=HELM_C128):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(LIB.helm_assemble_shared(ctx.handle, precision, ctypes.byref(h)))
+        self.handle = h
+        self.precision = precision
+        self.n = ctx.n
+
+    def close(self):
+        if self.handle:
+            LIB.helm_shared_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def helm_assemble_shared(ctx: Context, precision=HELM_C128) -> SharedOperator:
+    return SharedOperator(ctx, precision)
+
+
+def helm_spmv_multi(S: SharedOperator, freqs: Sequence[float], X: torch.Tensor, Y: torch.Tensor, stream=None):
+    """Y[f] = A(freqs[f]) X[f]; X, Y [nfreq, n] contiguous, complex in the precision of S."""
+    want = torch.complex64 if S.precision == HELM_C64 else torch.complex128
+    nf = len(freqs)
+    assert X.dtype == want and Y.dtype == want and X.is_contiguous() and Y.is_contiguous()
+    assert X.numel() == nf * S.n and Y.numel() == nf * S.n
+    fr = (ctypes.c_double * max(1, nf))(*[float(f) for f in freqs])
+    _check(LIB.helm_spmv_multi(S.handle, fr, nf, _ptr(X), _ptr(Y), _stream(stream)))
 
 
 def helm_reduce(op: int, x: torch.Tensor, y: Optional[torch.Tensor] = None, stream=None) -> complex:

@@ -34,7 +34,7 @@ def test_binding_names_match_header():
     assert sorted(helm.EXPORTED) == declared_functions()
     for n in declared_functions():
         if n in ("helm_destroy", "helm_matrix_free", "helm_last_error", "helm_sizes", "helm_matrix_csr",
-                 "helm_matrix_dia27"):
+                 "helm_matrix_dia27", "helm_shared_free"):
             continue
         assert hasattr(helm, n), n
 
