@@ -208,40 +208,6 @@ __device__ __forceinline__ cw dia_row_re_dw(const float2* __restrict__ vre, cons
   return out;
 }
 
-// The same product with the x neighbours taken from shared-memory windows: xs holds, for the
-// three lattice planes dl = -1, 0, 1, the x values of global indices cb + dl NxNy - Nx - 1 + t
-// (t < kXWin) of the row chunk that starts at cb; `local` = row - cb.
-constexpr int kXWin = 960;  // elements per plane window: kBlock + 2 Nx + 2 must fit
-__device__ __forceinline__ cw dia_row_re_dw_win(const float2* __restrict__ vre, const cw* xs, int64_t n, int Nx,
-                                                int local, int64_t row) {
-  dacc ar[3], ai[3];
-#pragma unroll
-  for (int dl = -1; dl <= 1; ++dl) {
-    float2 a[9];
-    cw xv[9];
-    const cw* w = xs + (dl + 1) * kXWin + local + Nx + 1;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const int di = q % 3 - 1, dj = q / 3 - 1;
-      a[q] = __ldcs(vre + (int64_t)(q + 9 * (dl + 1)) * n + row);
-      xv[q] = w[di + dj * Nx];
-    }
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      ar[q / 3].mac(a[q].x, a[q].y, xv[q].rh, xv[q].rl);
-      ai[q / 3].mac(a[q].x, a[q].y, xv[q].ih, xv[q].il);
-    }
-  }
-  ar[0].add(ar[1]);
-  ar[0].add(ar[2]);
-  ai[0].add(ai[1]);
-  ai[0].add(ai[2]);
-  cw out;
-  ar[0].get(out.rh, out.rl);
-  ai[0].get(out.ih, out.il);
-  return out;
-}
-
 // i Im(a) x part of a flagged row: re -= Im(a) x.im, im += Im(a) x.re
 __device__ __forceinline__ cw dia_row_im_dw(const float2* __restrict__ vim, const cw* x, int64_t n, int64_t Nx,
                                             int64_t NxNy, int64_t row) {

@@ -558,7 +558,7 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
 // per-thread dot-product partials converted to FP64 once per phase. Refinement residuals,
 // the correction x += ||r|| d and all scalar decisions stay FP64.
 
-__device__ void phaseA_dw(const KParams& P, int t, double* sh, cw* xs) {
+__device__ void phaseA_dw(const KParams& P, int t, double* sh) {
   const KTile T = P.tiles[t];
   KState* S = P.st + T.sys;
   if (!vload(&S->act)) return;
@@ -573,7 +573,7 @@ __device__ void phaseA_dw(const KParams& P, int t, double* sh, cw* xs) {
   auto first = [&](int64_t row, cw q, int c) {
     Y.qw[row] = q;
     const cw pi = src[row];
-    if (amode) Y.pw[row] = pi;  // (src is r here: the windows hold r, p is not read)
+    if (amode) Y.pw[row] = pi;
     if (!c) cw_dotu_acc(dr, di, pi, q);
   };
   auto fix = [&](int64_t row, cw qi) {
@@ -581,10 +581,7 @@ __device__ void phaseA_dw(const KParams& P, int t, double* sh, cw* xs) {
     Y.qw[row] = q;
     cw_dotu_acc(dr, di, src[row], q);
   };
-  if (P.xwin && kBlock + 2 * Y.Nx + 2 <= kXWin)
-    tile_spmv_dw_win(Y.valw, Y.cflag, src, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1, first, fix, P.prefetch, xs);
-  else
-    tile_spmv_dw(Y.valw, Y.cflag, src, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1, first, fix, P.prefetch);
+  tile_spmv_dw(Y.valw, Y.cflag, src, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1, first, fix, P.prefetch);
   double v[4] = {dr.to_double(), di.to_double(), 0.0, 0.0};
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
@@ -732,7 +729,6 @@ __device__ __forceinline__ bool in_fp64(const KParams& P, int t) {
 template <int PREC, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
   constexpr bool MIXED = PREC != 0;
-  __shared__ cw xs[PREC == 2 ? 3 * kXWin : 1];  // x windows of the double-word SpMV
   __shared__ double sh[4 * (kBlock / 32)];
   __shared__ int sh_int[kBlock / 32];
   const unsigned nb = gridDim.x;
@@ -748,7 +744,7 @@ __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
     if (blockIdx.x == 0) rebuilt = rebuild_list(P, cur, seen_fin, sh_int);
     for (int a = blockIdx.x; a < nat; a += nb) {
       if (PREC == 1 && !in_fp64(P, list[a])) phaseA_mixed(P, list[a], sh);
-      else if (PREC == 2 && !in_fp64(P, list[a])) phaseA_dw(P, list[a], sh, xs);
+      else if (PREC == 2 && !in_fp64(P, list[a])) phaseA_dw(P, list[a], sh);
       else phaseA_fp64(P, list[a], sh);
     }
     trace_mark(P, step, 0);

@@ -108,7 +108,6 @@ struct KParams {
   unsigned long long* trace;       // optional phase trace of block 0 (HELM_TRACE_STEPS), or null
   int trace_steps;
   int prefetch;                    // d > 0: prefetch each thread's row d rows-of-the-block ahead into L2
-  int xwin;                        // 1: double-word SpMV gathers x from shared-memory plane windows
 };
 
 
@@ -297,49 +296,6 @@ __device__ __forceinline__ void tile_spmv_dw(const float2* valw, const uint8_t* 
     const int c0 = cflag[r0];
     first(r0, s0, c0);
     has_c |= c0;
-  }
-  if (__syncthreads_or(has_c)) {
-    for (int64_t row = row0 + threadIdx.x; row < row1; row += kBlock)
-      if (cflag[row]) fix(row, dia_row_im_dw(vim, x, n, Nx, NxNy, row));
-  }
-}
-
-// tile_spmv_dw with the x neighbours staged in shared memory: per chunk of kBlock rows the block
-// loads, coalesced, the three plane windows of x the chunk's stencils touch (each x value once
-// instead of up to 9 times through L1/L2), then every row gathers from shared memory. Needs
-// kBlock + 2 Nx + 2 <= kXWin (the caller falls back to tile_spmv_dw otherwise) and xs of
-// 3 kXWin elements. Every thread of the block must call it (it synchronises the block).
-template <typename F1, typename F2>
-__device__ __forceinline__ void tile_spmv_dw_win(const float2* valw, const uint8_t* cflag, const cw* x, int64_t n,
-                                                 int64_t Nx, int64_t NxNy, int64_t row0, int64_t row1, F1 first,
-                                                 F2 fix, int pf, cw* xs) {
-  const float2* vim = valw + 27 * n;
-  int has_c = 0;
-  const int64_t ahead = (int64_t)pf * kBlock;
-  for (int64_t cb = row0; cb < row1; cb += kBlock) {
-    const int64_t ce = cb + kBlock < row1 ? cb + kBlock : row1;
-    const int len = (int)(ce - cb) + 2 * (int)Nx + 2;
-    __syncthreads();  // the previous chunk's rows have read their windows
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const int64_t lo = cb + (int64_t)(p - 1) * NxNy - Nx - 1;
-      for (int t = threadIdx.x; t < len; t += kBlock) {
-        int64_t g = lo + t;
-        g = g < 0 ? 0 : (g >= n ? n - 1 : g);  // outside the lattice: only padded slots (value 0) read it
-        xs[p * kXWin + t] = x[g];
-      }
-    }
-    __syncthreads();
-    const int64_t r0 = cb + threadIdx.x;
-    if (r0 < ce) {
-      if (pf && r0 + ahead < row1)
-#pragma unroll
-        for (int k = 0; k < 27; ++k) prefetch_l2(valw + (int64_t)k * n + r0 + ahead);
-      const cw s0 = dia_row_re_dw_win(valw, xs, n, (int)Nx, (int)threadIdx.x, r0);
-      const int c0 = cflag[r0];
-      first(r0, s0, c0);
-      has_c |= c0;
-    }
   }
   if (__syncthreads_or(has_c)) {
     for (int64_t row = row0 + threadIdx.x; row < row1; row += kBlock)

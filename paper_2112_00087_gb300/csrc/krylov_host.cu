@@ -217,10 +217,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   P.trace_steps = trace_steps;
   const char* pfenv = getenv("HELM_PREFETCH");  // tuning knob: prefetch distance in block rows, 0 = off
   P.prefetch = pfenv ? std::max(0, std::min(atoi(pfenv), 8)) : 1;
-  // tuning knob: 1 stages the double-word SpMV's x neighbours in shared-memory plane windows
-  // (measured slower on the sweep than gathering through L1: 21.2 vs 25.4 freqs/s), 0 = default
-  const char* xwenv = getenv("HELM_XWIN");
-  P.xwin = xwenv ? (atoi(xwenv) != 0) : 0;
+
   // Host-side fault injection for tests (never set in normal use): the barriers wait for one
   // block that does not exist and give up after 200 ms, so the launch ends with HELM_TIMEOUT
   // without faulting or hanging the GPU.
