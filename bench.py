@@ -41,8 +41,8 @@ TOL = 1e-10
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent launch of the
 # default benchmark step, from a single-pass ncu capture (profiles/traffic_sweep256.md), valid
 # only for the kernel sources it was taken on: reported as null once they change.
-TRAFFIC_CAPTURE = {"config": "sweep256/cocg/dw/jacobi", "sources_sha256_16": "24eb7218b4662d62",
-                   "bytes": 26894299593728 + 4993317558272}
+TRAFFIC_CAPTURE = {"config": "sweep256/cocg/dw/jacobi", "sources_sha256_16": "fd6396bdf642cb8e",
+                   "bytes": 26898163797760 + 4993768494848}
 KERNEL_SOURCES = ("paper_2112_00087_gb300/csrc/krylov_cocg.cu", "paper_2112_00087_gb300/csrc/krylov_engine.cuh",
                   "paper_2112_00087_gb300/csrc/kernels.cuh", "paper_2112_00087_gb300/csrc/dw.cuh",
                   "paper_2112_00087_gb300/csrc/common.cuh")
@@ -72,7 +72,7 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------------------
-# algorithmic bytes (what each solver step must move; see DESIGN.md)
+# algorithmic bytes (what each solver step must move)
 # ---------------------------------------------------------------------------------------------
 
 def spmv_bytes(n, nnz, vb):

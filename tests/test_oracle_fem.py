@@ -119,7 +119,7 @@ def test_rigid_box_eigenfrequencies_converge_at_h2():
         f_h = hi.C_SOUND / (2 * np.pi) * np.sqrt(lam_h(1, nx, 1.0 / nx))
         errs.append(abs(f_h - 170.0))
     assert 3.8 < errs[0] / errs[1] < 4.2 and 3.8 < errs[1] / errs[2] < 4.2
-    # the 20x16x12 lattice gives the survey's 170.17 Hz for (1,0,0)
+    # on the 20-cell axis of the 20x16x12 lattice the (1,0,0) mode sits at 170.17 Hz (continuum 170.0 Hz)
     f20 = hi.C_SOUND / (2 * np.pi) * np.sqrt(lam_h(1, 20, 0.05))
     assert abs(f20 - 170.17) < 0.01
 
