@@ -255,7 +255,7 @@ helm_status helm_solve_batch(helm_ctx* const* ctxs, const double* freqs_hz, int3
  *   p      (dev) complex128 [nfreq][n]: forward pressures from helm_solve at freqs_hz.
  *   w_node (dev) float64 [n]: listener weights (e.g. 1/|S| inside the listener region).
  * Because A is complex symmetric the adjoint system is A lam = W conj(p), solved with
- * `opts` (same solver as the forward solve). Outputs (PyTorch convention for a real loss:
+ * `opts` (any options helm_solve accepts: solver, precision mode, preconditioner). Outputs (PyTorch convention for a real loss:
  * d/dRe + i d/dIm), summed over frequencies:
  *   grad_beta (dev) complex128 [n_bface]: -2 conj(lam_F^T (i k rho c B_e) p) per boundary quad;
  *   grad_pdir (dev) complex128 [n_dir]  :  2 conj(W_D conj(p_D) - A_DF lam_F) per Dirichlet node

@@ -159,7 +159,7 @@ helm_status adjoint_grad(helm_ctx* ctx, const double* freqs, int nfreq, const he
   }
   std::vector<helm_solve_stats> stats(nfreq);
   if (st == HELM_OK) {
-    if (o.solver == HELM_SOLVER_COCG) {
+    if (o.solver != HELM_SOLVER_GMRES) {  // the persistent engine: COCG (any mode), BiCGSTAB, TFQMR
       std::vector<BatchSystem> sys(nfreq);
       for (int f = 0; f < nfreq; ++f) sys[f] = BatchSystem{ctx, freqs[f], lam + (size_t)f * n, &stats[f], rhs + (size_t)f * n};
       st = solve_cocg_batch(sys.data(), nfreq, o, s);

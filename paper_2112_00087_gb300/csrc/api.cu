@@ -337,8 +337,7 @@ helm_status helm_adjoint_grad(helm_ctx* c, const double* freqs_hz, int32_t nfreq
                               double* J_out) {
   if (!c || !freqs_hz || nfreq < 0 || !p || !w_node || !grad_beta || (c->n_dir > 0 && !grad_pdir))
     return set_error(HELM_ERR_ARG, "helm_adjoint_grad: bad argument");
-  if (!valid_opts(opts) || opts->mixed || opts->precond != HELM_PRECOND_NONE)
-    return set_error(HELM_ERR_ARG, "helm_adjoint_grad: invalid options (FP64, no preconditioner)");
+  if (!valid_opts(opts)) return set_error(HELM_ERR_ARG, "helm_adjoint_grad: invalid options");
   return adjoint_grad(c, freqs_hz, nfreq, *opts, (const cd*)p, w_node, nullptr, (cd*)grad_beta, (cd*)grad_pdir,
                       J_out);
 }
@@ -347,8 +346,7 @@ helm_status helm_adjoint_seed(helm_ctx* c, const double* freqs_hz, int32_t nfreq
                               const double* p, const double* grad_p, double* grad_beta, double* grad_pdir) {
   if (!c || !freqs_hz || nfreq < 0 || !p || !grad_p || !grad_beta || (c->n_dir > 0 && !grad_pdir))
     return set_error(HELM_ERR_ARG, "helm_adjoint_seed: bad argument");
-  if (!valid_opts(opts) || opts->mixed || opts->precond != HELM_PRECOND_NONE)
-    return set_error(HELM_ERR_ARG, "helm_adjoint_seed: invalid options (FP64, no preconditioner)");
+  if (!valid_opts(opts)) return set_error(HELM_ERR_ARG, "helm_adjoint_seed: invalid options");
   return adjoint_grad(c, freqs_hz, nfreq, *opts, (const cd*)p, nullptr, (const cd*)grad_p, (cd*)grad_beta,
                       (cd*)grad_pdir, nullptr);
 }

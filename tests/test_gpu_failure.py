@@ -22,11 +22,23 @@ def solve_ok(ctx):
     assert st[0]["status"] == 0 and st[0]["relres"] <= 1e-10
 
 
-def test_barrier_timeout_is_reported_and_the_context_survives():
+BARRIER_MODES = {
+    "cocg_fp64": dict(solver="cocg"),
+    "cocg_double_word_jacobi": dict(solver="cocg", mixed="dw", precond="jacobi", inner_tol=1e-12, inner_maxit=20000),
+    "bicgstab": dict(solver="bicgstab"),
+    "tfqmr_jacobi": dict(solver="tfqmr", precond="jacobi"),
+}
+
+
+@pytest.mark.parametrize("mode", list(BARRIER_MODES), ids=list(BARRIER_MODES))
+def test_barrier_timeout_is_reported_and_the_context_survives(mode):
+    # every persistent kernel (COCG in FP64 and double-word, BiCGSTAB, TFQMR's one-barrier state
+    # machine) gives up at its bounded grid barrier and returns HELM_TIMEOUT
     ctx = context(hi.small_box_problem())
     os.environ["HELM_FAULT_INJECT"] = "barrier"
     try:
-        p, st = helm.helm_solve(ctx, [100.0], helm.make_opts("cocg", tol=1e-10, maxit=20000), raise_on_fail=False)
+        p, st = helm.helm_solve(ctx, [100.0], helm.make_opts(tol=1e-10, maxit=20000, **BARRIER_MODES[mode]),
+                                raise_on_fail=False)
     finally:
         del os.environ["HELM_FAULT_INJECT"]
     assert st[0]["status"] == helm.HELM_TIMEOUT

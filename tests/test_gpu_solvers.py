@@ -231,6 +231,25 @@ def test_adjoint_matches_oracle_and_autograd():
     assert rel(pd.grad.cpu().numpy(), gdr) <= 1e-8
 
 
+def test_adjoint_with_the_benchmark_solver_options():
+    # forward and adjoint solves through the double-word inner COCG with FP64 refinement and
+    # symmetric Jacobi (right-hand sides of the adjoint scaled like b): same gradients as the
+    # oracle's direct solves, to the solve tolerance
+    prob = hi.cabin_problem(10, 7, 6, beta_seed=1, p_scale=0.1)
+    w = hi.listener_weights(prob.mesh, radius=0.45)
+    freqs = [60.0, 110.0]
+    ctx = context(prob)
+    o = helm.make_opts("cocg", tol=1e-12, maxit=20000, mixed="dw", inner_tol=1e-12, inner_maxit=20000,
+                       max_outer=20, precond="jacobi")
+    p, st = helm.helm_solve(ctx, freqs, o)
+    assert all(s["status"] == 0 for s in st)
+    J, gb, gd = helm.helm_adjoint_grad(ctx, freqs, o, p, torch.from_numpy(w).cuda())
+    Jr, gbr, gdr, _ = adjoint.objective_and_gradient(prob, freqs, w)
+    assert abs(J - Jr) <= 1e-9 * abs(Jr)
+    assert rel(gb.cpu().numpy(), gbr) <= 1e-7
+    assert rel(gd.cpu().numpy(), gdr) <= 1e-7
+
+
 def test_cocg_stagnation_restart_matches_oracle():
     # same restart rule on both sides: a small window forces several restarts
     prob = hi.small_box_problem(13, 7, 5)
