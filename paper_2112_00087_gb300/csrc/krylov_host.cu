@@ -14,9 +14,11 @@ namespace helm {
 namespace {
 using namespace eng;
 
-// Default minimum tile. Measured on the 256-frequency sweep (double-word mode): 512 / 2,048 /
-// 4,096 / 8,192 rows gave 25.8 / 28.3 / 31.8 / 31.5 freqs/s -- the per-tile reduction and
-// arrival cost of a phase outweighs load balance below a few thousand rows.
+// Default minimum tile, applied while the batch still gives every block about 8 tiles of that
+// size (a small batch keeps 512-row tiles so that all blocks have work). Measured on the
+// 256-frequency sweep (double-word mode): 512 / 2,048 / 4,096 / 8,192 rows gave 25.8 / 28.3 /
+// 31.8 / 31.5 freqs/s -- the per-tile reduction and arrival cost of a phase outweighs load
+// balance below a few thousand rows.
 constexpr int64_t kTileRowsMin = 4096;
 
 // Simple bump allocator over one device allocation (256-byte aligned pieces).
@@ -70,7 +72,11 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   // minimum tile (rows): each tile carries a block reduction and an arrival per phase, so small
   // systems are cut into few, larger tiles (tuning knob HELM_TILE_ROWS)
   const char* tenv_rows = getenv("HELM_TILE_ROWS");
-  const int64_t tile_min = TQ * std::max<int64_t>(1, ((tenv_rows ? atoll(tenv_rows) : (int64_t)kTileRowsMin) + TQ - 1) / TQ);
+  int64_t total_rows = 0;
+  for (int k = 0; k < nsys; ++k) total_rows += sys[k].ctx->n;
+  const int64_t tile_cap = TQ * std::max<int64_t>(1, total_rows / ((int64_t)nblocks * 8 * TQ));
+  const int64_t tile_req = tenv_rows ? atoll(tenv_rows) : std::min<int64_t>(kTileRowsMin, tile_cap);
+  const int64_t tile_min = TQ * std::max<int64_t>(1, (tile_req + TQ - 1) / TQ);
   for (int k = 0; k < nsys; ++k) {
     const int64_t n = sys[k].ctx->n;
     const int64_t per = std::max(tile_min, TQ * std::max<int64_t>(1, (n + TQ * nblocks - 1) / (TQ * nblocks)));

@@ -69,13 +69,15 @@ def test_bicgstab_early_iterates_match(k):
 
 
 def test_bicgstab_batch_of_different_meshes():
-    # (at 240 Hz on its sweep lattice BiCGSTAB with r0* = r0 = b breaks down: b lives on the
-    # sun-roof patch and its neighbours only, and (r0*, r) decays to 1e-22 there while the
-    # residual elsewhere is still 6e-4 -- a property of the method and of this shadow vector)
+    # Right-Jacobi BiCGSTAB (the paper's P-BiCGSTAB with P read as Jacobi) on three sweep
+    # lattices in one launch. Unpreconditioned BiCGSTAB with r0* = r0 = b breaks down on some
+    # sweep lattices depending on rounding (b lives on the sun-roof patch and its neighbours, and
+    # (r0*, r) decays to round-off there -- seen at 240 Hz, and at 140 Hz with another tiling),
+    # so the batch runs the preconditioned form; the unpreconditioned one is pinned above.
     freqs = [20.0, 60.0, 140.0]
     probs = [hi.cabin_problem(*hi.sweep_mesh_dims(f)) for f in freqs]
     ctxs = [context(pr) for pr in probs]
-    ps, st = helm.helm_solve_batch(ctxs, freqs, helm.make_opts("bicgstab", tol=1e-10, maxit=50000),
+    ps, st = helm.helm_solve_batch(ctxs, freqs, helm.make_opts("bicgstab", tol=1e-10, maxit=50000, precond="jacobi"),
                                    raise_on_fail=False)
     for k, (pr, f) in enumerate(zip(probs, freqs)):
         A, b = fem.system(pr, f)
@@ -83,7 +85,13 @@ def test_bicgstab_batch_of_different_meshes():
         assert st[k]["status"] == 0, (f, st[k])
         assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
         if pr.mesh.n_nodes < 60000:
-            assert in_range(st[k]["iterations"], count_range(A, b, 1e-10, seeds=(1, 2, 3)))
+            mv, _ = krylov.right_jacobi(A)
+            counts = [krylov.bicgstab(mv, b, tol=1e-10, maxit=50000)[1].iterations]
+            for sd in (1, 2, 3):
+                rng = np.random.default_rng(sd)
+                e = (rng.standard_normal(len(b)) + 1j * rng.standard_normal(len(b))) * 1e-14 * np.abs(b).max()
+                counts.append(krylov.bicgstab(mv, b + e, tol=1e-10, maxit=50000)[1].iterations)
+            assert in_range(st[k]["iterations"], (min(counts), max(counts))), (f, st[k], counts)
 
 
 def test_bicgstab_zero_rhs_and_single_brick():
