@@ -41,7 +41,8 @@ TOL = 1e-10
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent launch of the
 # default benchmark step, from a single-pass ncu capture (profiles/traffic_sweep256.md), valid
 # only for the kernel sources it was taken on: reported as null once they change.
-TRAFFIC_CAPTURE = {"config": "sweep256/cocg/dw/jacobi", "sources_sha256_16": "", "bytes": None}
+TRAFFIC_CAPTURE = {"config": "sweep256/cocg/dw/jacobi", "sources_sha256_16": "9cadfef4272ba4c5",
+                   "bytes": 27474689013248 + 4989292131328}
 KERNEL_SOURCES = ("paper_2112_00087_gb300/csrc/krylov_cocg.cu", "paper_2112_00087_gb300/csrc/krylov_engine.cuh",
                   "paper_2112_00087_gb300/csrc/kernels.cuh", "paper_2112_00087_gb300/csrc/dw.cuh",
                   "paper_2112_00087_gb300/csrc/common.cuh", "paper_2112_00087_gb300/csrc/krylov_host.cu")
