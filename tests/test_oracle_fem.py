@@ -219,3 +219,35 @@ def test_sign_of_admittance_is_dissipative():
     p = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
     val = np.vdot(p, A @ p)
     assert val.imag > 0
+
+
+def test_golden_box_modes_from_the_oracle_assembly():
+    """tests/golden/box_modes.json holds closed-form mode frequencies of the rigid test box and
+    cabin (written by tests/golden/make_box_modes.py from the formulas alone). The oracle's
+    assembled K, M reproduce the discrete ones (generalised eigenproblem) to 1e-9, and the
+    discrete values lie within 1% of the continuum ones at these lattices."""
+    import importlib.util
+    import json
+    import os
+
+    import scipy.sparse.linalg as spl
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    stored = json.load(open(os.path.join(here, "box_modes.json")))
+    spec = importlib.util.spec_from_file_location("make_box_modes", os.path.join(here, "make_box_modes.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    for name, (L, N) in gen.BOXES.items():
+        assert gen.modes(L, N) == stored["boxes"][name]["modes"]  # the fixture is the formula's output
+        mesh = hi.Mesh(N[0], N[1], N[2], *L)
+        K, M = fem.assemble_KM(mesh)
+        modes = stored["boxes"][name]["modes"]
+        fd = np.array([m["f_discrete"] for m in modes])
+        # shift-invert around the stored band; the rigid box has the constant mode at 0
+        sigma = (2 * np.pi * fd[0] * 0.5 / stored["c"]) ** 2
+        vals = spl.eigsh(K.tocsc(), k=len(fd) + 1, M=M.tocsc(), sigma=sigma, which="LM", return_eigenvectors=False)
+        f_oracle = np.sort(stored["c"] * np.sqrt(np.clip(vals, 0, None)) / (2 * np.pi))
+        f_oracle = f_oracle[f_oracle > 1.0][:len(fd)]
+        assert np.allclose(f_oracle, fd, rtol=1e-9, atol=0), (name, f_oracle, fd)
+        fc = np.array([m["f_continuum"] for m in modes])
+        assert np.all(np.abs(fd - fc) <= 0.01 * fc)
