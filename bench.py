@@ -539,6 +539,14 @@ def run_gpu(args):
                 helm.helm_solve_batch([c], [f], legs["fp64"][0], [o], raise_on_fail=False)
             torch.cuda.synchronize()
             out["fp64_sequential"] = {"freqs_per_s": nsys / (time.perf_counter() - t0), "precision": legs["fp64"][5]}
+        # the metric's comparison: batched main leg against plain FP64 COCG on the same GPU at
+        # the same accuracy (true rel-res 1e-10), with and without the main leg's preconditioner
+        out["speedups"] = {name: value / leg_["freqs_per_s"] for name, leg_ in
+                           (("vs_fp64_same_preconditioner_batched", out["legs"].get("fp64")),
+                            ("vs_fp64_unpreconditioned_batched", out["legs"].get("fp64_unpreconditioned")))
+                           if leg_ is not None}
+        if "fp64_sequential" in out:
+            out["speedups"]["vs_fp64_same_preconditioner_sequential"] = value / out["fp64_sequential"]["freqs_per_s"]
         out["spmv"] = spmv_roofline(helm, torch, peak_gbs)
 
         # end to end through host buffers: boundary data in from pinned memory, pressures out
@@ -687,6 +695,23 @@ def run_configs(args):
     print(json.dumps({"configs": res}), flush=True)
 
 
+def run_autotune(args):
+    """Coordinate search of the launch-shape knobs for the main leg on the chosen workload."""
+    import torch
+    from paper_2112_00087_gb300 import autotune, helm
+    freqs, probs, ctxs, outs = build_sweep(args.nfreq, helm, torch, args.workload)
+    pc = None if args.precond == "none" else args.precond
+    opts = {"fp64": fp64_opts, "c64": mixed_opts, "dw": dw_opts}["c64" if args.mixed else args.precision](helm, args.maxit, pc)
+
+    def run():
+        helm.helm_solve_batch(ctxs, freqs, opts, outs, raise_on_fail=False)
+        return helm.helm_last_profile()["solve_ms"] / 1e3
+
+    run()  # warm-up
+    best, log = autotune.autotune(run)
+    print(json.dumps({"autotune": {"best": best, "trials": [{"config": c, "solve_s": t} for c, t in log]}}), flush=True)
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -735,11 +760,15 @@ def main():
                     help="Jacobi preconditioning (symmetric for COCG, right for BiCGSTAB / TFQMR)")
     ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
     ap.add_argument("--configs", action="store_true", help="measure the secondary workloads instead")
+    ap.add_argument("--autotune", action="store_true",
+                    help="search the persistent engine's launch-shape knobs on this workload (one line of JSON)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes (read + write) of one persistent launch from an ncu capture, if known")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.autotune:
+        run_autotune(args)
     elif args.configs:
         run_configs(args)
     else:

@@ -1,0 +1,85 @@
+"""Launch-shape autotuner for the persistent batched solver.
+
+The persistent engine reads three launch-shape knobs from the environment at every solve:
+``HELM_PERSIST_BLOCKS_PER_SM`` (resident blocks per SM, i.e. the register budget),
+``HELM_TILE_ROWS`` (minimum rows per tile, i.e. how many per-tile reductions a phase pays) and
+``HELM_PREFETCH`` (L2 prefetch distance of the streamed matrix, in block rows). ``autotune``
+searches them coordinate by coordinate for a caller-supplied workload: the caller passes a
+function that runs one solve under the current environment and returns its time in seconds
+(for example CUDA-event time of ``helm_solve_batch``), and gets back the fastest setting found,
+which ``apply`` installs for later solves of the process.
+
+The search is plain coordinate descent from the library defaults: each knob in turn is set to
+each of its candidate values with the others held, the best value is kept, and passes repeat
+until a pass changes nothing (or ``max_passes``). Every candidate is timed ``reps`` times and
+scored by its minimum.
+"""
+from __future__ import annotations
+
+import os
+from typing import Callable, Dict, List, Optional, Sequence, Tuple
+
+DEFAULTS: Dict[str, int] = {"HELM_PERSIST_BLOCKS_PER_SM": 2, "HELM_TILE_ROWS": 4096, "HELM_PREFETCH": 1}
+SPACE: Dict[str, Sequence[int]] = {
+    "HELM_PERSIST_BLOCKS_PER_SM": (1, 2, 3),
+    "HELM_TILE_ROWS": (512, 2048, 4096, 8192),
+    "HELM_PREFETCH": (0, 1, 2),
+}
+
+
+def apply(config: Dict[str, int]) -> None:
+    """Install a setting for the solves that follow in this process."""
+    for k, v in config.items():
+        os.environ[k] = str(int(v))
+
+
+def _timed(run: Callable[[], float], config: Dict[str, int], reps: int) -> float:
+    saved = {k: os.environ.get(k) for k in config}
+    try:
+        apply(config)
+        return min(float(run()) for _ in range(reps))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def autotune(run: Callable[[], float], space: Optional[Dict[str, Sequence[int]]] = None,
+             start: Optional[Dict[str, int]] = None, reps: int = 1,
+             max_passes: int = 3) -> Tuple[Dict[str, int], List[Tuple[Dict[str, int], float]]]:
+    """Coordinate-descent search over `space` (default SPACE) from `start` (default DEFAULTS).
+
+    run() executes one solve under the current environment and returns its time in seconds.
+    Returns (best setting, [(setting, time) for every setting timed, in order]). The process
+    environment is left as it was; call apply(best) to use the result."""
+    space = dict(SPACE if space is None else space)
+    best = dict(DEFAULTS if start is None else start)
+    for k in space:
+        best.setdefault(k, space[k][0])
+    seen: Dict[Tuple[Tuple[str, int], ...], float] = {}
+    log: List[Tuple[Dict[str, int], float]] = []
+
+    def score(cfg: Dict[str, int]) -> float:
+        key = tuple(sorted(cfg.items()))
+        if key not in seen:
+            seen[key] = _timed(run, cfg, reps)
+            log.append((dict(cfg), seen[key]))
+        return seen[key]
+
+    best_t = score(best)
+    for _ in range(max_passes):
+        changed = False
+        for knob, values in space.items():
+            for v in values:
+                if v == best[knob]:
+                    continue
+                cand = dict(best)
+                cand[knob] = v
+                t = score(cand)
+                if t < best_t:
+                    best, best_t, changed = cand, t, True
+        if not changed:
+            break
+    return best, log
