@@ -28,8 +28,9 @@
  *
  * Conventions for every entry point:
  *   - Pointers marked (dev) are device pointers of the current CUDA device, (host) host ones.
- *   - The caller owns every buffer it passes; the library owns helm_ctx / helm_matrix and the
- *     scratch they allocate (freed by helm_destroy / helm_matrix_free).
+ *   - The caller owns every buffer it passes; the library owns helm_ctx / helm_matrix /
+ *     helm_shared and the scratch they allocate (freed by helm_destroy / helm_matrix_free /
+ *     helm_shared_free).
  *   - Work is ordered on the stream given to helm_create (or to helm_spmv); calls return
  *     without synchronising unless stated otherwise.
  *   - A non-HELM_OK status comes with a message from helm_last_error(). No C++ exception
@@ -53,7 +54,8 @@ typedef enum {
   HELM_ERR_CUDA = 2,       /* a CUDA runtime call failed */
   HELM_ERR_OOM = 3,        /* device allocation failed */
   HELM_NOT_CONVERGED = 4,  /* solve hit maxit; best iterate and stats are still written */
-  HELM_BREAKDOWN = 5,      /* Krylov breakdown (COCG p^T A p == 0 or r^T r == 0) */
+  HELM_BREAKDOWN = 5,      /* Krylov breakdown (COCG p^T A p == 0 or r^T r == 0; BiCGSTAB / TFQMR
+                              (r0*, v) == 0, rho == 0 or omega == 0) */
   HELM_NAN = 6,            /* non-finite residual */
   HELM_PIVOT = 7,          /* Schwarz local factorisation met a pivot below threshold */
   HELM_TIMEOUT = 8,        /* a device-side wait gave up (bounded barrier) */
@@ -116,7 +118,8 @@ typedef struct {
 typedef struct {
   int32_t status;       /* helm_status of this system */
   int32_t iterations;   /* Krylov steps (inner steps included when mixed) */
-  int32_t restarts;     /* GMRES cycles - 1 / COCG residual-replacement restarts */
+  int32_t restarts;     /* GMRES cycles - 1 / COCG, BiCGSTAB, TFQMR restarts after a missed
+                           true-residual check */
   int32_t outer;        /* mixed: refinement steps taken */
   double relres;        /* true FP64 ||b - A p|| / ||b|| at exit */
   double bnorm;         /* ||b||_2 */
@@ -134,7 +137,7 @@ typedef struct {
 } helm_profile;
 
 typedef struct helm_ctx helm_ctx;       /* one lattice + physics + boundary data */
-typedef struct helm_matrix helm_matrix; /* one assembled, eliminated system matrix (CSR) */
+typedef struct helm_matrix helm_matrix; /* one assembled, eliminated system matrix (CSR or DIA27) */
 typedef struct helm_shared helm_shared; /* frequency-independent parts K, M, B of a lattice */
 
 /* Last error message of the calling thread ("" if none). Owned by the library. */
