@@ -38,6 +38,10 @@ by step in complex128 numpy, the two iterations the GPU path runs:
   rho = (w, r0*), beta, u = w + beta u and v = A u + beta (A u_old + beta v). The bound
   ||r_m|| <= tau sqrt(m + 1) is the stopping estimate; then the true residual decides, and a
   miss restarts from x. Iteration count = steps m (one product with A per step on average).
+* ``pcocg``: COCG with a diagonal preconditioner in the classical preconditioned-CG form
+  (z = D^-1 r, rho = r^T z, p = z + beta p); in exact arithmetic its iterates equal those of COCG
+  on S A S (S = D^-1/2) mapped back by x = S y, the form ``sym_jacobi`` builds -- an independent
+  formulation used to cross-check that one.
 * ``right_jacobi``: the "P" of the paper's P-BiCGSTAB / P-TFQMR read as Jacobi, applied on the
   right (A D^-1 y = b, x = D^-1 y, D = diag(A)), so residuals stay those of A x = b.
 
@@ -373,3 +377,41 @@ def sym_jacobi(A):
     s = 1.0 / np.sqrt(d)
     S = sp.diags(s)
     return (S @ A @ S).tocsr(), s, np.abs(d)
+
+
+def pcocg(matvec, b, dinv, tol=1e-10, maxit=100000):
+    """COCG preconditioned by the diagonal dinv (z = dinv * r), x0 = 0, stop on the true-system
+    residual estimate ||r|| / ||b|| <= tol (no restarts). Returns (x, Stats)."""
+    b = np.asarray(b, dtype=np.complex128)
+    dinv = np.asarray(dinv, dtype=np.complex128)
+    x = np.zeros_like(b)
+    st = Stats()
+    nb = nrm2(b)
+    if nb == 0:
+        st.converged, st.relres = True, 0.0
+        return x, st
+    r = b.copy()
+    z = dinv * r
+    p = z.copy()
+    rho = dotu(r, z)
+    while st.iterations < maxit:
+        q = matvec(p)
+        st.iterations += 1
+        mu = dotu(p, q)
+        if mu == 0 or rho == 0:
+            st.breakdown = True
+            break
+        alpha = rho / mu
+        x = x + alpha * p
+        r = r - alpha * q
+        est = nrm2(r) / nb
+        st.history.append(est)
+        if est <= tol:
+            break
+        z = dinv * r
+        rho_new = dotu(r, z)
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+    st.relres = nrm2(b - matvec(x)) / nb
+    st.converged = st.relres <= tol
+    return x, st

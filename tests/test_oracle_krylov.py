@@ -224,3 +224,25 @@ def test_weighted_norm_cocg_with_unit_weights_is_plain_cocg():
     x1, s1 = krylov.cocg(lambda v: A @ v, b, tol=1e-10)
     x2, s2 = krylov.cocg(lambda v: A @ v, b, tol=1e-10, weights=np.ones(len(b)))
     assert s1.iterations == s2.iterations and np.array_equal(x1, x2)
+
+
+def test_sym_jacobi_form_equals_preconditioned_cocg():
+    # two formulations of Jacobi-preconditioned COCG: S A S with weighted norms (what the GPU
+    # runs) and classical preconditioned COCG with z = D^-1 r. Same iterates up to rounding and
+    # the same residual history, step by step.
+    prob = hi.small_box_problem(10, 8, 6)
+    A, b = fem.system(prob, 150.0)
+    Ah, s, w = krylov.sym_jacobi(A)
+    dinv = 1.0 / A.diagonal()
+    for k in (1, 2, 5):
+        y, st1 = krylov.cocg(lambda v: Ah @ v, s * b, tol=1e-300, maxit=k, weights=w)
+        x, st2 = krylov.pcocg(lambda v: A @ v, b, dinv, tol=1e-300, maxit=k)
+        assert np.linalg.norm(s * y - x) <= 1e-11 * np.linalg.norm(x)
+    # later iterates drift apart along ill-conditioned directions (1e-2 at step 20 here) while the
+    # residual histories, which both forms measure on A x = b, still agree to rounding
+    _, st1 = krylov.cocg(lambda v: Ah @ v, s * b, tol=1e-300, maxit=40, weights=w)
+    _, st2 = krylov.pcocg(lambda v: A @ v, b, dinv, tol=1e-300, maxit=40)
+    assert np.allclose(st1.history, st2.history, rtol=1e-8, atol=0)
+    _, st1 = krylov.cocg(lambda v: Ah @ v, s * b, tol=1e-10, weights=w)
+    _, st2 = krylov.pcocg(lambda v: A @ v, b, dinv, tol=1e-10)
+    assert abs(st1.iterations - st2.iterations) <= 1 and st2.converged
