@@ -77,11 +77,10 @@ def test_multi_frequency_argument_errors():
     ctx = context(hi.small_box_problem(6, 4, 3))
     S = helm.helm_assemble_shared(ctx, helm.HELM_C128)
     X = torch.zeros(2, ctx.n, dtype=torch.complex128, device="cuda")
-    with pytest.raises(helm.HelmError):
-        helm.LIB.helm_spmv_multi  # noqa: B018 (the raw call below checks X == Y)
+    with pytest.raises(helm.HelmError):  # X and Y overlap
         helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 2)(1.0, 2.0), 2,
                                              helm._ptr(X), helm._ptr(X), None))
-    with pytest.raises(helm.HelmError):
+    with pytest.raises(helm.HelmError):  # negative frequency
         helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 1)(-5.0), 1,
                                              helm._ptr(X), helm._ptr(X[1:]), None))
     # an empty batch is a no-op
