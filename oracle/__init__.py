@@ -13,7 +13,6 @@ Modules (paper sections they follow):
   krylov   -- restarted GMRES(m) with complex Givens, COCG (Sec. 4: Krylov solve, complex FP64)
   ras      -- restricted additive Schwarz with exact local solves (Sec. 4: overlapping Schwarz DD)
   adjoint  -- listener objective and its gradient by an adjoint solve
-  ir       -- FP64 iterative refinement around a complex64 inner solve
 
 Parity status per function is stated in each module header.
 """

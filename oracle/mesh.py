@@ -5,7 +5,10 @@ structured box lattice: node id = i + (nx+1)(j + (ny+1) l); brick (i,j,l) has lo
 vertices (a,b,c) in {0,1}^3 numbered a + 2b + 4c; boundary quads are numbered side by
 side x-, x+, y-, y+, z-, z+ and, inside a side, by u + nu*v over the two remaining axes
 (first remaining axis fastest). Pinned by tests/test_oracle_fem.py (assembled matrices
-equal the Kronecker closed form, which depends on this numbering).
+equal the Kronecker closed form, which depends on this numbering) and, quad by quad and side
+by side, by tests/test_oracle_boundary.py (face mass of every side equals its Kronecker
+closed form; single quads land on the nodes the numbering names; admittance ducts along
+every axis equal the exact 1D solution).
 """
 import numpy as np
 
