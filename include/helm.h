@@ -189,7 +189,7 @@ helm_status helm_matrix_csr(const helm_matrix* A, int64_t* n, int64_t* nnz, int3
  * parts, layout above). HELM_ERR_ARG for CSR. */
 helm_status helm_matrix_dia27(const helm_matrix* A, int64_t* n, int32_t* precision, const void** val);
 
-/* y = A x (paper Sec. 4: "the most time consuming operation") for either layout. x, y (dev)
+/* y = A x (paper Sec. 4: the SpMV dominates the cost of a Krylov step) for either layout. x, y (dev)
  * complex [n] in the matrix precision (complex64 matrices accumulate in FP32), must not overlap. Ordered on
  * `stream` (cudaStream_t; NULL = the context stream of the matrix). */
 helm_status helm_spmv(const helm_matrix* A, const void* x, void* y, void* stream);
@@ -228,7 +228,9 @@ helm_status helm_reduce(int32_t op, int64_t n, const double* x, const double* y,
  *   - n may be at most 16,777,216 (4096 partial sums of 4096 elements); larger n returns
  *     HELM_ERR_ARG with a message naming the limit.
  *   - The first call on a device looks up the array's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *     that device current); make that first call before any stream capture. The address is
+ *     cached for the life of the process: after cudaDeviceReset (or any teardown of the
+ *     device's primary context) this entry point must not be called again in that process.
  *   - Every call shares the array and overwrites what it uses; calls that overlap on the GPU
  *     (concurrent streams, threads) race and must be serialised by the caller.
  * Results agree with helm_reduce to rounding (the partial sums are grouped differently);

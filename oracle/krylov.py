@@ -415,3 +415,85 @@ def pcocg(matvec, b, dinv, tol=1e-10, maxit=100000):
     st.relres = nrm2(b - matvec(x)) / nb
     st.converged = st.relres <= tol
     return x, st
+
+
+def cocg_ir(matvec, b, tol=1e-10, inner_tol=1e-12, inner_maxit=100000, max_outer=20, maxit=100000, stall=None,
+            weights=None):
+    """Iterative refinement around an inner COCG, all in complex128: the outer loop of the
+    mixed-precision solves, stated with an FP64 inner solve. Returns (x, Stats, outer) where
+    Stats.iterations counts inner COCG steps and ``outer`` the refinement steps (negative when
+    the refinement stalled and the system was solved by plain COCG from zero instead).
+
+    Outer step: r = b - A x; stop when ||r|| / ||b|| <= tol (true residual), or after max_outer
+    steps or maxit inner steps; if a refinement step did not halve the residual of the previous
+    one, fall back to ``cocg`` from x = 0 for the rest of the budget. Otherwise solve A d = r / ||r||
+    by COCG from d = 0 (no restarts) until its residual estimate reaches
+    max(inner_tol, tol ||b|| / (2 ||r||)) -- so one inner solve can reach the outer target with a
+    margin of two -- or inner_maxit / maxit steps, a breakdown, or ``stall`` steps without a
+    halving of its best estimate; then x += ||r|| d, unless the inner solve did not reduce its
+    residual at all (estimate >= 1), in which case the correction is dropped. Norms are weighted
+    by ``weights`` as in ``cocg``.
+    """
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    if weights is not None:
+        w = np.asarray(weights, dtype=np.float64)
+        nrm = lambda v: math.sqrt(math.fsum(w * (v.real * v.real + v.imag * v.imag)))  # noqa: E731
+    else:
+        nrm = nrm2
+    x = np.zeros(n, dtype=np.complex128)
+    st = Stats()
+    outer = 0
+    nb = nrm(b)
+    if nb == 0:
+        st.converged, st.relres = True, 0.0
+        return x, st, outer
+    prev = 1.0
+    while True:
+        r = b - matvec(x)
+        rel = nrm(r) / nb
+        st.relres = rel
+        if rel <= tol:
+            st.converged = True
+            return x, st, outer
+        if outer >= max_outer or st.iterations >= maxit:
+            return x, st, outer
+        if outer >= 1 and rel > 0.5 * prev:
+            x, st2 = cocg(matvec, b, tol=tol, maxit=maxit - st.iterations, stall=stall, weights=weights)
+            st.iterations += st2.iterations
+            st.restarts += st2.restarts
+            st.converged, st.relres, st.breakdown = st2.converged, st2.relres, st2.breakdown
+            st.history += st2.history
+            return x, st, -outer
+        prev = rel
+        rn = rel * nb
+        outer += 1
+        target = max(inner_tol, 0.5 * tol * nb / rn)
+        s = r / rn
+        d = np.zeros(n, dtype=np.complex128)
+        p = s.copy()
+        rho = dotu(s, s)
+        best, best_it, k, est = 1.0, 0, 0, 1.0
+        while True:
+            q = matvec(p)
+            k += 1
+            st.iterations += 1
+            mu = dotu(p, q)
+            if mu == 0 or rho == 0:
+                st.breakdown = True
+                break
+            alpha = rho / mu
+            d = d + alpha * p
+            s = s - alpha * q
+            est = nrm(s)
+            st.history.append(est * rel)
+            if est < 0.5 * best:
+                best, best_it = est, k
+            if (est <= target or k >= inner_maxit or st.iterations >= maxit
+                    or (stall and k - best_it >= stall)):
+                break
+            rho_new = dotu(s, s)
+            p = s + (rho_new / rho) * p
+            rho = rho_new
+        if est < 1.0:
+            x = x + rn * d

@@ -153,7 +153,13 @@ helm_status helm_spmv_multi(const helm_shared* S, const double* freqs_hz, int32_
                             void* stream) {
   if (!S || !freqs_hz || nfreq < 0 || (nfreq > 0 && (!X || !Y)))
     return set_error(HELM_ERR_ARG, "helm_spmv_multi: bad argument");
-  if (nfreq > 0 && X == Y) return set_error(HELM_ERR_ARG, "helm_spmv_multi: X and Y must not overlap");
+  if (nfreq > 0) {
+    // byte ranges [X, X + nfreq n vb) and [Y, Y + nfreq n vb) must be disjoint
+    const size_t vb = S->precision == HELM_C64 ? 8 : 16;
+    const uintptr_t x0 = (uintptr_t)X, y0 = (uintptr_t)Y, len = (uintptr_t)((size_t)nfreq * (size_t)S->n * vb);
+    if (len > 0 && x0 < y0 + len && y0 < x0 + len)
+      return set_error(HELM_ERR_ARG, "helm_spmv_multi: X and Y must not overlap");
+  }
   for (int f = 0; f < nfreq; ++f)
     if (!(freqs_hz[f] >= 0.0)) return set_error(HELM_ERR_ARG, "helm_spmv_multi: negative or NaN frequency");
   if (nfreq == 0 || S->n == 0) return HELM_OK;

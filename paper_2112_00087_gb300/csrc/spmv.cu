@@ -1,4 +1,4 @@
-// Standalone SpMV (paper Sec. 4: CSR storage; SpMV "the most time consuming operation") and
+// Standalone SpMV (paper Sec. 4: CSR storage; the SpMV dominates the Krylov iteration cost) and
 // deterministic FP64 reductions (dot products / norms of the Krylov methods).
 #include <algorithm>
 #include <mutex>
@@ -212,9 +212,12 @@ helm_status reduce_c128_noalloc(int op, int64_t n, const cd* x, const cd* y, dou
   helm_status st = noalloc_scratch(&buf);
   if (st != HELM_OK) return st;
   const int nparts = (int)((n + kNoAllocChunk - 1) / kNoAllocChunk);
+  // an error left by earlier, unrelated work is reported as such, not as a launch failure here
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "helm_reduce_noalloc: error pending before the call");
   reduce_stage1<<<nparts, kBlock, 0, s>>>(op, x, y, n, kNoAllocChunk, buf);
   reduce_stage2<<<1, kBlock, 0, s>>>(buf, nparts, buf + 2 * kNoAllocMaxParts);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out_host, buf + 2 * kNoAllocMaxParts, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

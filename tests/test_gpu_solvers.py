@@ -125,6 +125,24 @@ def test_gmres_matches_oracle(dims, f, m):
     assert rel(p[0].cpu().numpy(), x) <= 1e-9
 
 
+def test_gmres_stagnation_matches_oracle():
+    # GMRES(10) on the 13x7x5 box at 230 Hz stagnates (the oracle reaches rel-res 2.3e-8 after
+    # 20,000 steps), so it is compared after a fixed budget: 600 steps (60 restart cycles), where
+    # the trajectory is stable under rounding-level changes (oracle with CGS2 / MGS and with b
+    # perturbed at 1e-14: rel-res 4.97212e-3 to 8 digits, iterates within 3e-8 of each other)
+    prob = hi.small_box_problem(13, 7, 5)
+    ctx = context(prob)
+    A, b = fem.system(prob, 230.0)
+    p, st = helm.helm_solve(ctx, [230.0], helm.make_opts("gmres", restart=10, tol=1e-10, maxit=600),
+                            raise_on_fail=False)
+    x, ost = krylov.gmres(lambda v: A @ v, b, 10, tol=1e-10, maxit=600)
+    assert st[0]["status"] == helm.HELM_NOT_CONVERGED and not ost.converged
+    assert st[0]["iterations"] == ost.iterations == 600
+    assert within5(st[0]["restarts"], ost.restarts)
+    assert abs(st[0]["relres"] - ost.relres) <= 1e-6 * ost.relres
+    assert rel(p[0].cpu().numpy(), x) <= 1e-6
+
+
 @pytest.mark.parametrize("dims,parts,f", [((12, 10, 8), (3, 2, 2), 200.0), ((25, 14, 12), (4, 2, 2), 100.0),
                                           ((6, 5, 4), (1, 1, 1), 150.0)])
 def test_gmres_ras_matches_oracle(dims, parts, f):

@@ -80,9 +80,18 @@ def test_multi_frequency_argument_errors():
     with pytest.raises(helm.HelmError):  # X and Y overlap
         helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 2)(1.0, 2.0), 2,
                                              helm._ptr(X), helm._ptr(X), None))
+    # partial overlap: Y starts inside X (one frequency), valid frequencies
+    X3 = torch.zeros(3, ctx.n, dtype=torch.complex128, device="cuda")
+    with pytest.raises(helm.HelmError):
+        helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 2)(1.0, 2.0), 2,
+                                             helm._ptr(X3), helm._ptr(X3[1:]), None))
+    # adjacent, not overlapping: accepted
+    helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 1)(1.0), 1,
+                                         helm._ptr(X3[0:1]), helm._ptr(X3[1:2]), None))
+    torch.cuda.synchronize()
     with pytest.raises(helm.HelmError):  # negative frequency
         helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 1)(-5.0), 1,
-                                             helm._ptr(X), helm._ptr(X[1:]), None))
+                                             helm._ptr(X3[0:1]), helm._ptr(X3[2:3]), None))
     # an empty batch is a no-op
     helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 1)(1.0), 0, None, None, None))
     S.close()

@@ -246,3 +246,62 @@ def test_sym_jacobi_form_equals_preconditioned_cocg():
     _, st1 = krylov.cocg(lambda v: Ah @ v, s * b, tol=1e-10, weights=w)
     _, st2 = krylov.pcocg(lambda v: A @ v, b, dinv, tol=1e-10)
     assert abs(st1.iterations - st2.iterations) <= 1 and st2.converged
+
+
+@pytest.mark.parametrize("dims,f", [((3, 2, 2), 150.0), ((6, 4, 3), 230.0), ((10, 8, 6), 100.0)])
+def test_refined_cocg_matches_dense_lu(dims, f):
+    prob = hi.small_box_problem(*dims)
+    A, b = fem.system(prob, f)
+    ref = np.linalg.solve(A.toarray(), b)
+    Ah, s, w = krylov.sym_jacobi(A)
+    y, st, outer = krylov.cocg_ir(lambda v: Ah @ v, s * b, tol=1e-12, weights=w)
+    x = s * y
+    assert st.converged and outer >= 1
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert np.linalg.norm(b - A @ x) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_refined_cocg_first_inner_solve_is_cocg_to_half_the_tolerance():
+    # In FP64 the first inner solve (from d = 0 on r / ||r|| = b / ||b||) is COCG on b up to a
+    # scaling of every vector by 1 / ||b||; with the inner target tol / 2 it takes the steps plain
+    # COCG takes to reach tol / 2, and its result already meets tol, so one refinement step ends.
+    for dims, f in (((10, 8, 6), 100.0), ((13, 7, 5), 230.0)):
+        prob = hi.small_box_problem(*dims)
+        A, b = fem.system(prob, f)
+        Ah, s, w = krylov.sym_jacobi(A)
+        mv = lambda v: Ah @ v
+        _, st_ir, outer = krylov.cocg_ir(mv, s * b, tol=1e-10, weights=w)
+        _, st_c = krylov.cocg(mv, s * b, tol=0.5e-10, weights=w)
+        assert outer == 1 and st_ir.converged
+        assert abs(st_ir.iterations - st_c.iterations) <= 1, (st_ir.iterations, st_c.iterations)
+        # same residual history step by step (rounding of the 1 / ||b|| scaling only)
+        # (the erratic history amplifies rounding later on)
+        assert np.allclose(st_ir.history[:20], st_c.history[:20], rtol=1e-9, atol=0)
+
+
+def test_refined_cocg_outer_residual_is_the_inner_estimate():
+    # with an FP64 inner solve the correction is applied exactly (up to rounding): after each
+    # refinement step the true relative residual equals the inner solve's final estimate times
+    # the relative residual it started from; capped inner solves need several refinement steps
+    prob = hi.small_box_problem(6, 4, 3)
+    A, b = fem.system(prob, 10.0)
+    prev = 1.0
+    for mo in (1, 2, 3):
+        _, st, outer = krylov.cocg_ir(lambda v: A @ v, b, tol=1e-12, inner_maxit=8, max_outer=mo)
+        assert outer == mo and st.iterations == 8 * mo and not st.converged
+        assert abs(st.relres - st.history[-1]) <= 1e-9 * st.relres  # history holds est * rel_start
+        assert st.relres < 0.5 * prev
+        prev = st.relres
+
+
+def test_refined_cocg_falls_back_to_cocg_when_refinement_stalls():
+    # the fourth capped inner solve of this system does not reduce its residual: the correction
+    # is dropped, the refinement stalls and hands the system to plain COCG from zero, whose
+    # result it returns unchanged
+    prob = hi.small_box_problem(6, 4, 3)
+    A, b = fem.system(prob, 10.0)
+    x, st, outer = krylov.cocg_ir(lambda v: A @ v, b, tol=1e-12, inner_maxit=8)
+    xc, stc = krylov.cocg(lambda v: A @ v, b, tol=1e-12)
+    assert outer == -4 and st.converged
+    assert st.iterations == 32 + stc.iterations
+    assert np.array_equal(x, xc)

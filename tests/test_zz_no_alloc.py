@@ -53,3 +53,25 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = helm.LIB.helm_reduce_noalloc(2, n, ctypes.c_void_p(x.data_ptr()), None, out, None)
     assert st == helm.HELM_ERR_ARG
     assert b"16777216" in helm.LIB.helm_last_error()
+
+
+def test_noalloc_needs_no_device_allocation():
+    # with every device allocation of the library failing (host-side injection, no GPU fault),
+    # helm_reduce reports HELM_ERR_OOM while helm_reduce_noalloc still gives the same result
+    import os
+    n = 50_001
+    x = torch.from_numpy(hi.random_complex(n, seed=21)).cuda()
+    y = torch.from_numpy(hi.random_complex(n, seed=22)).cuda()
+    ref = c_abi("helm_reduce", 1, x, y)
+    before = c_abi("helm_reduce_noalloc", 1, x, y)
+    os.environ["HELM_FAULT_INJECT"] = "oom"
+    try:
+        out = (ctypes.c_double * 2)()
+        st = helm.LIB.helm_reduce(1, n, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), out,
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == helm.HELM_ERR_OOM
+        during = c_abi("helm_reduce_noalloc", 1, x, y)
+    finally:
+        del os.environ["HELM_FAULT_INJECT"]
+    assert during == before
+    assert abs(during - ref) <= 1e-14 * float((x.abs() * y.abs()).sum())
