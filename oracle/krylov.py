@@ -417,8 +417,37 @@ def pcocg(matvec, b, dinv, tol=1e-10, maxit=100000):
     return x, st
 
 
+def cocg_inner(matvec, s, target, inner_maxit, maxit_left, stall, nrm):
+    """The inner solve of ``cocg_ir``: COCG on A d = s from d = 0, no restarts, in complex128.
+    Stops when the residual estimate nrm(s_k) reaches `target`, after inner_maxit or maxit_left
+    steps, on a breakdown, or after `stall` steps without a halving of its best estimate.
+    Returns (d, steps, final estimate, breakdown, estimate history)."""
+    d = np.zeros_like(s)
+    p = s.copy()
+    rho = dotu(s, s)
+    best, best_it, k, est, hist = 1.0, 0, 0, 1.0, []
+    while True:
+        q = matvec(p)
+        k += 1
+        mu = dotu(p, q)
+        if mu == 0 or rho == 0:
+            return d, k, est, True, hist
+        alpha = rho / mu
+        d = d + alpha * p
+        s = s - alpha * q
+        est = nrm(s)
+        hist.append(est)
+        if est < 0.5 * best:
+            best, best_it = est, k
+        if est <= target or k >= inner_maxit or k >= maxit_left or (stall and k - best_it >= stall):
+            return d, k, est, False, hist
+        rho_new = dotu(s, s)
+        p = s + (rho_new / rho) * p
+        rho = rho_new
+
+
 def cocg_ir(matvec, b, tol=1e-10, inner_tol=1e-12, inner_maxit=100000, max_outer=20, maxit=100000, stall=None,
-            weights=None):
+            weights=None, inner=None):
     """Iterative refinement around an inner COCG, all in complex128: the outer loop of the
     mixed-precision solves, stated with an FP64 inner solve. Returns (x, Stats, outer) where
     Stats.iterations counts inner COCG steps and ``outer`` the refinement steps (negative when
@@ -432,7 +461,8 @@ def cocg_ir(matvec, b, tol=1e-10, inner_tol=1e-12, inner_maxit=100000, max_outer
     margin of two -- or inner_maxit / maxit steps, a breakdown, or ``stall`` steps without a
     halving of its best estimate; then x += ||r|| d, unless the inner solve did not reduce its
     residual at all (estimate >= 1), in which case the correction is dropped. Norms are weighted
-    by ``weights`` as in ``cocg``.
+    by ``weights`` as in ``cocg``. ``inner`` replaces the FP64 inner solve (``cocg_inner``'s
+    signature and results), e.g. by one in another arithmetic.
     """
     b = np.asarray(b, dtype=np.complex128)
     n = b.shape[0]
@@ -441,6 +471,8 @@ def cocg_ir(matvec, b, tol=1e-10, inner_tol=1e-12, inner_maxit=100000, max_outer
         nrm = lambda v: math.sqrt(math.fsum(w * (v.real * v.real + v.imag * v.imag)))  # noqa: E731
     else:
         nrm = nrm2
+    solve_inner = inner if inner is not None else (lambda s_, t_, im_, ml_, st_, nm_: cocg_inner(
+        matvec, s_, t_, im_, ml_, st_, nm_))
     x = np.zeros(n, dtype=np.complex128)
     st = Stats()
     outer = 0
@@ -469,31 +501,9 @@ def cocg_ir(matvec, b, tol=1e-10, inner_tol=1e-12, inner_maxit=100000, max_outer
         rn = rel * nb
         outer += 1
         target = max(inner_tol, 0.5 * tol * nb / rn)
-        s = r / rn
-        d = np.zeros(n, dtype=np.complex128)
-        p = s.copy()
-        rho = dotu(s, s)
-        best, best_it, k, est = 1.0, 0, 0, 1.0
-        while True:
-            q = matvec(p)
-            k += 1
-            st.iterations += 1
-            mu = dotu(p, q)
-            if mu == 0 or rho == 0:
-                st.breakdown = True
-                break
-            alpha = rho / mu
-            d = d + alpha * p
-            s = s - alpha * q
-            est = nrm(s)
-            st.history.append(est * rel)
-            if est < 0.5 * best:
-                best, best_it = est, k
-            if (est <= target or k >= inner_maxit or st.iterations >= maxit
-                    or (stall and k - best_it >= stall)):
-                break
-            rho_new = dotu(s, s)
-            p = s + (rho_new / rho) * p
-            rho = rho_new
+        d, k, est, bd, hist = solve_inner(r / rn, target, inner_maxit, maxit - st.iterations, stall, nrm)
+        st.iterations += k
+        st.breakdown = st.breakdown or bd
+        st.history += [h * rel for h in hist]
         if est < 1.0:
             x = x + rn * d
