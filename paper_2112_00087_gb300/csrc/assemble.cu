@@ -272,13 +272,21 @@ __global__ void cast_real_kernel(const double* __restrict__ v, float* __restrict
 }
 
 // Double-word copy of m doubles: out[t] = (hi, lo), hi = fl32(v), lo = fl32(v - hi).
-__global__ void split_kernel(const double* __restrict__ v, float2* __restrict__ out, int64_t m) {
+// Double-word copy of `nslots` FP64 slot arrays of n values each (slot stride n) into (hi, lo)
+// float pairs with slot stride ns >= n; the ns - n padding entries of every slot are zero.
+__global__ void split_kernel(const double* __restrict__ v, float2* __restrict__ out, int64_t n, int64_t ns,
+                             int64_t m) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (; t < m; t += stride) {
-    const double a = v[t];
-    const float hi = __double2float_rn(a);
-    out[t] = make_float2(hi, __double2float_rn(a - (double)hi));
+  for (; t < m; t += stride) {  // m = nslots * ns
+    const int64_t k = t / ns, row = t - k * ns;
+    float2 o = make_float2(0.f, 0.f);
+    if (row < n) {
+      const double a = v[k * n + row];
+      const float hi = __double2float_rn(a);
+      o = make_float2(hi, __double2float_rn(a - (double)hi));
+    }
+    out[t] = o;
   }
 }
 
@@ -294,10 +302,11 @@ helm_status assemble_components(const helm_ctx* ctx, double* comp, float* comp32
   return HELM_OK;
 }
 
-helm_status split_values(const double* val, float2* out, int64_t m, cudaStream_t s) {
+helm_status split_values(const double* val, float2* out, int64_t n, int64_t ns, int nslots, cudaStream_t s) {
+  const int64_t m = (int64_t)nslots * ns;
   if (m == 0) return HELM_OK;
   int blocks = (int)std::min<int64_t>((m + 255) / 256, 152 * 16);
-  split_kernel<<<blocks, 256, 0, s>>>(val, out, m);
+  split_kernel<<<blocks, 256, 0, s>>>(val, out, n, ns, m);
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }

@@ -127,8 +127,9 @@ helm_status cast_values(const cd* val, cf* val32, int64_t nnz, cudaStream_t s);
 // frequency-independent parts [K | M | Re B | Im B] (each 27 n, slot-major) of the eliminated
 // matrix, their FP32 copy (if comp32 != null) and the rows with a wall term
 helm_status assemble_components(const helm_ctx* ctx, double* comp, float* comp32, uint8_t* bflag, cudaStream_t s);
-// double-word (hi, lo) float pairs of m doubles
-helm_status split_values(const double* val, float2* out, int64_t m, cudaStream_t s);
+// double-word (hi, lo) float pairs of nslots slot arrays of n doubles, written with slot stride ns >= n
+// (padding entries zero)
+helm_status split_values(const double* val, float2* out, int64_t n, int64_t ns, int nslots, cudaStream_t s);
 
 // spmv.cu
 helm_status spmv_c128(const int32_t* rowptr, const int32_t* col, const cd* val, const cd* x, cd* y,

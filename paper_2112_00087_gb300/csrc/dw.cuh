@@ -109,4 +109,83 @@ __device__ __forceinline__ void cw_dotu_acc(dacc& re, dacc& im, const cw& x, con
   im.mac(x.ih, x.il, y.rh, y.rl);
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Packed form: two independent double-word accumulations (in practice the real and the
+// imaginary component of one complex value) carried in float2 registers and advanced with the
+// paired FP32 instructions of sm_100-class GPUs (__ffma2_rn, __fadd2_rn, __fmul2_rn: two
+// correctly rounded FP32 operations per instruction). Every component follows exactly the
+// operation sequence of `dacc` above, so results are bitwise those of two scalar accumulators;
+// subtractions are written as fma(b, -1, a) = fl(a - b) and the product error as the sum of
+// ah*xh and the exact negation of its rounded value, so no separate negation is needed.
+// ---------------------------------------------------------------------------------------------
+namespace dw2 {
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+}  // namespace dw2
+
+struct dacc2 {
+  float2 s, c;  // component k holds the double-word value s.k + c.k
+  __device__ __forceinline__ dacc2() : s(make_float2(0.f, 0.f)), c(make_float2(0.f, 0.f)) {}
+  // += (ah + al)(xh + xl) per component (the scalar mac with the same operations): exact head
+  // product, low-order cross terms into c
+  __device__ __forceinline__ void mac(float2 ah, float2 al, float2 xh, float2 xl) {
+    using namespace dw2;
+    const float2 np = mul(f2(-ah.x, -ah.y), xh);  // -fl(ah xh), exactly
+    float2 e = fma(ah, xh, np);                    // ah xh - fl(ah xh)
+    e = fma(ah, xl, e);
+    e = fma(al, xh, e);
+    // TwoSum(s, p) with p = -np: s2 = fl(s + p), bb = fl(s2 - s) (kept negated: nbb = fl(s - s2))
+    const float2 s2 = sub(s, np);
+    const float2 nbb = sub(s, s2);
+    const float2 da = sub(s, dw2::add(s2, nbb));  // s - (s2 - bb)
+    const float2 db = sub(nbb, np);               // p - bb
+    const float2 t = dw2::add(da, db);
+    s = s2;
+    c = dw2::add(c, dw2::add(t, e));
+  }
+  // += (h + l) per component
+  __device__ __forceinline__ void add(float2 h, float2 l) {
+    using namespace dw2;
+    const float2 s2 = dw2::add(s, h);
+    const float2 bb = sub(s2, s);
+    const float2 t = dw2::add(sub(s, sub(s2, bb)), sub(h, bb));
+    s = s2;
+    c = dw2::add(c, dw2::add(t, l));
+  }
+  __device__ __forceinline__ void add(const dacc2& o) { add(o.s, o.c); }
+  // normalised (hi, lo) per component (FastTwoSum of s and c)
+  __device__ __forceinline__ void get(float2& hi, float2& lo) const {
+    using namespace dw2;
+    hi = dw2::add(s, c);
+    lo = sub(c, sub(hi, s));
+  }
+};
+
+// complex double-word value as the packed pair of its components' heads and tails
+__device__ __forceinline__ float2 cw_hi(const cw& v) { return make_float2(v.rh, v.ih); }
+__device__ __forceinline__ float2 cw_lo(const cw& v) { return make_float2(v.rl, v.il); }
+__device__ __forceinline__ cw cw_from(float2 hi, float2 lo) { return cw{hi.x, lo.x, hi.y, lo.y}; }
+
+// y + a x, bitwise equal to cw_axpy: per component re = yr + ar xr - ai xi, im = yi + ar xi + ai xr
+__device__ __forceinline__ cw cw_axpy2(const cw& y, const cws& a, const cw& x) {
+  dacc2 acc;
+  acc.s = cw_hi(y);
+  acc.c = cw_lo(y);
+  acc.mac(make_float2(a.rh, a.rh), make_float2(a.rl, a.rl), cw_hi(x), cw_lo(x));
+  acc.mac(make_float2(-a.ih, a.ih), make_float2(-a.il, a.il), make_float2(x.ih, x.rh), make_float2(x.il, x.rl));
+  float2 hi, lo;
+  acc.get(hi, lo);
+  return cw_from(hi, lo);
+}
+
+// (re, im) += x^T y, bitwise equal to cw_dotu_acc on (re, im)
+__device__ __forceinline__ void cw_dotu_acc2(dacc2& acc, const cw& x, const cw& y) {
+  acc.mac(make_float2(x.rh, x.rh), make_float2(x.rl, x.rl), cw_hi(y), cw_lo(y));
+  acc.mac(make_float2(-x.ih, x.ih), make_float2(-x.il, x.il), make_float2(y.ih, y.rh), make_float2(y.il, y.rl));
+}
+
 }  // namespace helm

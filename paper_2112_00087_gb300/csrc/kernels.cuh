@@ -173,59 +173,24 @@ __device__ __forceinline__ cplx<T> dia_row_im(const T* __restrict__ vim, const c
   return acc;
 }
 
-// Double-word versions of the two passes (matrix parts as (hi, lo) float pairs in the same
-// slot-major split layout, vectors as complex double-word): the products and sums run on the
-// FP32 pipe with Dot2-style error accumulation, three accumulators per component as above.
-__device__ __forceinline__ cw dia_row_re_dw(const float2* __restrict__ vre, const cw* x, int64_t n, int64_t Nx,
-                                            int64_t NxNy, int64_t row) {
-  dacc ar[3], ai[3];
-#pragma unroll
-  for (int dl = -1; dl <= 1; ++dl) {
-    float2 a[9];
-    cw xv[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const int di = q % 3 - 1, dj = q / 3 - 1;
-      const int k = q + 9 * (dl + 1);
-      int64_t c = row + di + Nx * dj + NxNy * dl;
-      c = c < 0 ? 0 : (c >= n ? n - 1 : c);
-      a[q] = __ldcs(vre + (int64_t)k * n + row);
-      xv[q] = x[c];
-    }
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      ar[q / 3].mac(a[q].x, a[q].y, xv[q].rh, xv[q].rl);
-      ai[q / 3].mac(a[q].x, a[q].y, xv[q].ih, xv[q].il);
-    }
-  }
-  ar[0].add(ar[1]);
-  ar[0].add(ar[2]);
-  ai[0].add(ai[1]);
-  ai[0].add(ai[2]);
-  cw out;
-  ar[0].get(out.rh, out.rl);
-  ai[0].get(out.ih, out.il);
-  return out;
-}
-
-// i Im(a) x part of a flagged row: re -= Im(a) x.im, im += Im(a) x.re
-__device__ __forceinline__ cw dia_row_im_dw(const float2* __restrict__ vim, const cw* x, int64_t n, int64_t Nx,
-                                            int64_t NxNy, int64_t row) {
-  dacc ar, ai;
+// Double-word i Im(a) x part of a row flagged complex (imaginary matrix parts as (hi, lo) float
+// pairs, slot-major with slot stride ns >= n): re -= Im(a) x.im, im += Im(a) x.re, Dot2-style
+// accumulation on the FP32 pipe, both components in one packed accumulator.
+__device__ __forceinline__ cw dia_row_im_dw2(const float2* __restrict__ vim, const cw* x, int64_t n, int64_t ns,
+                                             int64_t Nx, int64_t NxNy, int64_t row) {
+  dacc2 acc;
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
     const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dl = k / 9 - 1;
     int64_t c = row + di + Nx * dj + NxNy * dl;
     c = c < 0 ? 0 : (c >= n ? n - 1 : c);
-    const float2 b = vim[(int64_t)k * n + row];
+    const float2 b = vim[(int64_t)k * ns + row];
     const cw xv = x[c];
-    ar.mac(-b.x, -b.y, xv.ih, xv.il);
-    ai.mac(b.x, b.y, xv.rh, xv.rl);
+    acc.mac(make_float2(-b.x, b.x), make_float2(-b.y, b.y), make_float2(xv.ih, xv.rh), make_float2(xv.il, xv.rl));
   }
-  cw out;
-  ar.get(out.rh, out.rl);
-  ai.get(out.ih, out.il);
-  return out;
+  float2 hi, lo;
+  acc.get(hi, lo);
+  return cw_from(hi, lo);
 }
 
 // Deterministic block sum of NV doubles per thread (fixed shuffle tree, then warps in order).

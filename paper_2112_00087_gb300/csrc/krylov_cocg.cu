@@ -555,8 +555,82 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
 // ------------------------------- double-word mixed phases -------------------------------------
 // Same refinement as above; the inner COCG runs in double-word arithmetic (dw.cuh): matrix,
 // vectors and every inner product and update carried as pairs of floats on the FP32 pipe, the
-// per-thread dot-product partials converted to FP64 once per phase. Refinement residuals,
-// the correction x += ||r|| d and all scalar decisions stay FP64.
+// real and imaginary components of each complex value advanced together by the paired FP32
+// instructions (dacc2), the per-thread dot-product partials converted to FP64 once per phase.
+// Refinement residuals, the correction x += ||r|| d and all scalar decisions stay FP64.
+
+// Real-part product of one row in double-word arithmetic: matrix parts (slot stride ns) and x
+// by cached loads, three accumulators per component (one per stencil line dj), planes in order.
+// CLAMP: gather indices clamped into [0, n) (rows whose stencil reaches outside the index range;
+// the entries there are zero); interior rows skip the clamps.
+template <bool CLAMP>
+__device__ __forceinline__ cw dia_row_re_dw2(const float2* __restrict__ vre, const cw* x, int64_t n, int64_t ns,
+                                             int64_t Nx, int64_t NxNy, int64_t row) {
+  dacc2 acc[3];
+#pragma unroll
+  for (int dl = -1; dl <= 1; ++dl) {
+    float2 a[9];
+    cw xv[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {  // all loads of one lattice plane first
+      const int di = q % 3 - 1, dj = q / 3 - 1;
+      const int k = q + 9 * (dl + 1);
+      int64_t c = row + di + Nx * dj + NxNy * dl;
+      if (CLAMP) c = c < 0 ? 0 : (c >= n ? n - 1 : c);
+      a[q] = __ldcs(vre + (int64_t)k * ns + row);
+      xv[q] = x[c];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      acc[q / 3].mac(make_float2(a[q].x, a[q].x), make_float2(a[q].y, a[q].y), cw_hi(xv[q]), cw_lo(xv[q]));
+  }
+  acc[0].add(acc[1]);
+  acc[0].add(acc[2]);
+  float2 hi, lo;
+  acc[0].get(hi, lo);
+  return cw_from(hi, lo);
+}
+
+// Product of the tile's rows with x: first(row, q, complex_row_flag) with the real-part product
+// of every row, then, if any row of the tile is flagged complex, fix(row, imaginary part) for the
+// flagged rows. With `pf` = d > 0 each thread prefetches into L2 the matrix parts of the row it
+// reaches d iterations later.
+template <typename F1, typename F2>
+__device__ __forceinline__ void tile_spmv_dw(const KSys& Y, const cw* x, int64_t row0, int64_t row1, F1 first, F2 fix,
+                                             int pf) {
+  const int64_t n = Y.n, ns = Y.nsw, Nx = Y.Nx, NxNy = Y.NxNy;
+  const int64_t reach = NxNy + Nx + 1;  // largest |column - row| of the stencil
+  int has_c = 0;
+  const int64_t ahead = (int64_t)pf * kBlock;
+  for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += kBlock) {
+    if (pf && r0 + ahead < row1)
+#pragma unroll
+      for (int k = 0; k < 27; ++k) prefetch_l2(Y.valw + (int64_t)k * ns + r0 + ahead);
+    const cw s0 = (r0 >= reach && r0 + reach < n) ? dia_row_re_dw2<false>(Y.valw, x, n, ns, Nx, NxNy, r0)
+                                                  : dia_row_re_dw2<true>(Y.valw, x, n, ns, Nx, NxNy, r0);
+    const int c0 = Y.cflag[r0];
+    first(r0, s0, c0);
+    has_c |= c0;
+  }
+  if (__syncthreads_or(has_c)) {
+    const float2* vim = Y.valw + 27 * ns;
+    for (int64_t row = row0 + threadIdx.x; row < row1; row += kBlock)
+      if (Y.cflag[row]) fix(row, dia_row_im_dw2(vim, x, n, ns, Nx, NxNy, row));
+  }
+}
+
+// Thread 0: bulk L2 prefetch of rows [r0, r0 + kBlock) of the given vectors (16 bytes per row).
+template <int NV>
+__device__ __forceinline__ void prefetch_rows(const cw* const (&v)[NV], int64_t r0, int64_t row1) {
+  if (r0 >= row1) return;
+  const uint32_t bytes = (uint32_t)((row1 - r0 < kBlock ? row1 - r0 : kBlock) * 16);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) bulk_prefetch_l2(v[k] + r0, bytes);
+}
+
+__device__ __forceinline__ double2 dacc2_to_double(const dacc2& a) {
+  return make_double2((double)a.s.x + (double)a.c.x, (double)a.s.y + (double)a.c.y);
+}
 
 __device__ void phaseA_dw(const KParams& P, int t, double* sh) {
   const KTile T = P.tiles[t];
@@ -569,20 +643,21 @@ __device__ void phaseA_dw(const KParams& P, int t, double* sh) {
   }
   const int amode = vload(&S->amode);
   const cw* src = amode ? Y.rw : Y.pw;
-  dacc dr, di;  // p^T q
+  dacc2 dot;  // p^T q
   auto first = [&](int64_t row, cw q, int c) {
     Y.qw[row] = q;
     const cw pi = src[row];
     if (amode) Y.pw[row] = pi;
-    if (!c) cw_dotu_acc(dr, di, pi, q);
+    if (!c) cw_dotu_acc2(dot, pi, q);
   };
   auto fix = [&](int64_t row, cw qi) {
     const cw q = cw_add(Y.qw[row], qi);
     Y.qw[row] = q;
-    cw_dotu_acc(dr, di, src[row], q);
+    cw_dotu_acc2(dot, src[row], q);
   };
-  tile_spmv_dw(Y.valw, Y.cflag, src, Y.n, Y.Nx, Y.NxNy, T.row0, T.row1, first, fix, P.prefetch);
-  double v[4] = {dr.to_double(), di.to_double(), 0.0, 0.0};
+  tile_spmv_dw(Y, src, T.row0, T.row1, first, fix, P.prefetch);
+  const double2 d2 = dacc2_to_double(dot);
+  double v[4] = {d2.x, d2.y, 0.0, 0.0};
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
   if (arrive_last(S, Y.ntiles)) {
@@ -616,7 +691,7 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
     }
     // start an inner solve on r / ||r|| (double-word), d = 0
     const double sc = 1.0 / S->rnorm;
-    dacc rr_, ri_;
+    dacc2 rr;
     for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
       const cd ri = Y.r[i];
       cw w;
@@ -624,9 +699,10 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
       split_double(ri.im * sc, w.ih, w.il);
       Y.rw[i] = w;
       Y.xw[i] = cw{0.f, 0.f, 0.f, 0.f};
-      cw_dotu_acc(rr_, ri_, w, w);
+      cw_dotu_acc2(rr, w, w);
     }
-    double v[4] = {rr_.to_double(), ri_.to_double(), 0.0, 0.0};
+    const double2 r2 = dacc2_to_double(rr);
+    double v[4] = {r2.x, r2.y, 0.0, 0.0};
     block_sum<4>(v, sh);
     write_parts(P.part, t, v);
     if (arrive_last(S, Y.ntiles)) {
@@ -646,32 +722,54 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
   const cd al = S->alpha;
   const cws a = to_cws(al.re, al.im);
   const cws ma = to_cws(-al.re, -al.im);
-  dacc rr_, ri_;
+  dacc2 rr;
   float nrm = 0.f;  // ||r||^2 for the stopping estimate (FP32 is enough for a threshold test)
-  for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-    const int64_t ia = i + (int64_t)P.prefetch * kBlock;
-    if (P.prefetch && ia < T.row1) {
-      prefetch_l2(Y.pw + ia);
-      prefetch_l2(Y.qw + ia);
-      prefetch_l2(Y.xw + ia);
-      prefetch_l2(Y.rw + ia);
+  // thread 0 keeps the block's next `pf_chunks` row chunks of p, q, x, r on their way into L2
+  const int d = P.pf_chunks;
+  const cw* const vecs[4] = {Y.pw, Y.qw, Y.xw, Y.rw};
+  if (threadIdx.x == 0)
+    for (int j = 0; j < d; ++j) prefetch_rows(vecs, T.row0 + (int64_t)j * kBlock, T.row1);
+  // HELM_VEC_UNROLL rows per thread per pass, all of their loads issued before the arithmetic
+  constexpr int U = HELM_VEC_UNROLL;
+  for (int64_t i0 = T.row0; i0 < T.row1; i0 += U * kBlock) {
+    if (threadIdx.x == 0 && d > 0)
+#pragma unroll
+      for (int u = 0; u < U; ++u) prefetch_rows(vecs, i0 + (int64_t)(d + u) * kBlock, T.row1);
+    cw pv[U], qv[U], xv[U], rv[U];
+    float wv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
+      if (i < T.row1) {
+        pv[u] = Y.pw[i];
+        qv[u] = Y.qw[i];
+        xv[u] = Y.xw[i];
+        rv[u] = Y.rw[i];
+        wv[u] = wnorm32(Y, i);
+      }
     }
-    const cw pv = Y.pw[i], qv = Y.qw[i];
-    const cw xn = cw_axpy(Y.xw[i], a, pv);
-    const cw rn = cw_axpy(Y.rw[i], ma, qv);
-    Y.xw[i] = xn;
-    Y.rw[i] = rn;
-    cw_dotu_acc(rr_, ri_, rn, rn);
-    nrm = fmaf(wnorm32(Y, i), fmaf(rn.rh, rn.rh, rn.ih * rn.ih), nrm);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
+      if (i < T.row1) {
+        const cw xn = cw_axpy2(xv[u], a, pv[u]);
+        const cw rn = cw_axpy2(rv[u], ma, qv[u]);
+        Y.xw[i] = xn;
+        Y.rw[i] = rn;
+        cw_dotu_acc2(rr, rn, rn);
+        nrm = fmaf(wv[u], fmaf(rn.rh, rn.rh, rn.ih * rn.ih), nrm);
+      }
+    }
   }
-  double v[4] = {rr_.to_double(), ri_.to_double(), (double)nrm, 0.0};
+  const double2 r2 = dacc2_to_double(rr);
+  double v[4] = {r2.x, r2.y, (double)nrm, 0.0};
   block_sum<4>(v, sh);
   write_parts(P.part, t, v);
   if (arrive_last(S, Y.ntiles)) {
-    cd rho_new, rr;
-    sum_parts(P.part, Y.tile0, Y.ntiles, rho_new, rr, sh);
+    cd rho_new, rrn;
+    sum_parts(P.part, Y.tile0, Y.ntiles, rho_new, rrn, sh);
     if (threadIdx.x == 0) {
-      const double est = sqrt(rr.re);  // relative to ||r / ||r|| || = 1
+      const double est = sqrt(rrn.re);  // relative to ||r / ||r|| || = 1
       S->est = est;
       S->amode = 0;
       if (est < 0.5 * S->best_est) {
@@ -703,7 +801,30 @@ __device__ void phaseC_dw(const KParams& P, int t, double* sh) {
   if (vload(&S->cmode) == C_PUPDATE) {
     const cd be = S->beta;
     const cws b = to_cws(be.re, be.im);
-    for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) Y.pw[i] = cw_axpy(Y.rw[i], b, Y.pw[i]);
+    const int d = P.pf_chunks;
+    const cw* const vecs[2] = {Y.rw, Y.pw};
+    if (threadIdx.x == 0)
+      for (int j = 0; j < d; ++j) prefetch_rows(vecs, T.row0 + (int64_t)j * kBlock, T.row1);
+    constexpr int U = HELM_VEC_UNROLL;
+    for (int64_t i0 = T.row0; i0 < T.row1; i0 += U * kBlock) {
+      if (threadIdx.x == 0 && d > 0)
+#pragma unroll
+        for (int u = 0; u < U; ++u) prefetch_rows(vecs, i0 + (int64_t)(d + u) * kBlock, T.row1);
+      cw rv[U], pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
+        if (i < T.row1) {
+          rv[u] = Y.rw[i];
+          pv[u] = Y.pw[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
+        if (i < T.row1) Y.pw[i] = cw_axpy2(rv[u], b, pv[u]);
+      }
+    }
     return;
   }
   // refinement update x += ||r|| d (FP64)
@@ -742,28 +863,29 @@ __global__ void __launch_bounds__(kBlock, MINB) cocg_persistent(KParams P) {
     const int* list = cur ? P.list1 : P.list0;
     bool rebuilt = false;
     if (blockIdx.x == 0) rebuilt = rebuild_list(P, cur, seen_fin, sh_int);
-    for (int a = blockIdx.x; a < nat; a += nb) {
-      if (PREC == 1 && !in_fp64(P, list[a])) phaseA_mixed(P, list[a], sh);
-      else if (PREC == 2 && !in_fp64(P, list[a])) phaseA_dw(P, list[a], sh);
-      else phaseA_fp64(P, list[a], sh);
-    }
+    for_tiles_dynamic(P, 3 * step, nat, list, [&](int t) {
+      if (PREC == 1 && !in_fp64(P, t)) phaseA_mixed(P, t, sh);
+      else if (PREC == 2 && !in_fp64(P, t)) phaseA_dw(P, t, sh);
+      else phaseA_fp64(P, t, sh);
+    });
     trace_mark(P, step, 0);
+    trace_count(P, step, nat);
     if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
     trace_mark(P, step, 1);
     if (rebuilt && threadIdx.x == 0) P.ctrl[CTRL_CUR] = cur ^ 1;
-    for (int a = blockIdx.x; a < nat; a += nb) {
-      if (PREC == 1 && !in_fp64(P, list[a])) phaseB_mixed(P, list[a], sh);
-      else if (PREC == 2 && !in_fp64(P, list[a])) phaseB_dw(P, list[a], sh);
-      else phaseB_fp64(P, list[a], sh);
-    }
+    for_tiles_dynamic(P, 3 * step + 1, nat, list, [&](int t) {
+      if (PREC == 1 && !in_fp64(P, t)) phaseB_mixed(P, t, sh);
+      else if (PREC == 2 && !in_fp64(P, t)) phaseB_dw(P, t, sh);
+      else phaseB_fp64(P, t, sh);
+    });
     trace_mark(P, step, 2);
     if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
     trace_mark(P, step, 3);
-    for (int a = blockIdx.x; a < nat; a += nb) {
-      if (PREC == 1 && !in_fp64(P, list[a])) phaseC_mixed(P, list[a], sh);
-      else if (PREC == 2 && !in_fp64(P, list[a])) phaseC_dw(P, list[a], sh);
-      else phaseC_fp64(P, list[a], sh);
-    }
+    for_tiles_dynamic(P, 3 * step + 2, nat, list, [&](int t) {
+      if (PREC == 1 && !in_fp64(P, t)) phaseC_mixed(P, t, sh);
+      else if (PREC == 2 && !in_fp64(P, t)) phaseC_dw(P, t, sh);
+      else phaseC_fp64(P, t, sh);
+    });
     trace_mark(P, step, 4);
     if (!grid_barrier(P.bar, nb, P.bar_extra, P.bar_timeout)) return;
     trace_mark(P, step, 5);

@@ -5,6 +5,7 @@
 // mixed) and krylov_bicg.cu (BiCGSTAB, TFQMR); krylov_host.cu launches them.
 #pragma once
 
+#include "bulk.cuh"
 #include "kernels.cuh"
 
 namespace helm {
@@ -25,7 +26,8 @@ struct KSys {
   cf* r32;
   cf* p32;
   cf* q32;
-  const float2* valw;  // double-word mixed mode: (hi, lo) pairs, slot-major split layout
+  const float2* valw;  // double-word mixed mode: (hi, lo) pairs, slot-major split layout, slot stride nsw
+  int64_t nsw;         // slot stride of valw: n rounded up to even (16-byte aligned slot starts)
   cw* xw;
   cw* rw;
   cw* pw;
@@ -82,9 +84,11 @@ struct KTile {
   int64_t row0, row1;
 };
 
-// CTRL_P0 / CTRL_P1: tile list used on even / odd super-steps (engines with one barrier per step)
+// CTRL_P0 / CTRL_P1: tile list used on even / odd super-steps (engines with one barrier per step);
+// CTRL_Q0 .. CTRL_Q0 + 5: tile counters of the dynamically scheduled phases (one per phase, six
+// in rotation)
 enum : int { CTRL_CUR = 0, CTRL_CNT0 = 1, CTRL_CNT1 = 2, CTRL_NACT = 3, CTRL_FIN = 4, CTRL_P0 = 5, CTRL_P1 = 6,
-             CTRL_N = 8 };
+             CTRL_Q0 = 8, CTRL_NQ = 6, CTRL_N = 16 };
 
 struct KParams {
   const KSys* sys;
@@ -107,7 +111,10 @@ struct KParams {
   unsigned long long bar_timeout;  // barrier give-up time (ns)
   unsigned long long* trace;       // optional phase trace of block 0 (HELM_TRACE_STEPS), or null
   int trace_steps;
-  int prefetch;                    // d > 0: prefetch each thread's row d rows-of-the-block ahead into L2
+  int prefetch;                    // double-word SpMV: each thread prefetches into L2 the matrix parts of
+                                   // the row it reaches this many block rows later (0 = off)
+  int pf_chunks;                   // double-word vector phases: thread 0 bulk-prefetches into L2 the
+                                   // vectors of the block's chunk of 256 rows this many chunks ahead
 };
 
 
@@ -138,14 +145,46 @@ __device__ __forceinline__ double wnorm(const KSys& Y, int64_t i) { return Y.wn 
 __device__ __forceinline__ float wnorm32(const KSys& Y, int64_t i) { return Y.wn32 ? Y.wn32[i] : 1.f; }
 
 // Phase trace (tracing aid, off unless HELM_TRACE_STEPS is set): block 0 records %globaltimer
-// after its own work of each phase and after each grid barrier, for the first trace_steps steps.
+// after its own work of each phase and after each grid barrier, for the first trace_steps steps
+// (kTraceStride slots per step: six times, then the number of active tiles of the step).
+constexpr int kTraceStride = 8;
 __device__ __forceinline__ void trace_mark(const KParams& P, int step, int k) {
   if (P.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && step < P.trace_steps)
-    P.trace[(size_t)step * 6 + k] = globaltimer();
+    P.trace[(size_t)step * kTraceStride + k] = globaltimer();
+}
+__device__ __forceinline__ void trace_count(const KParams& P, int step, int nat) {
+  if (P.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && step < P.trace_steps)
+    P.trace[(size_t)step * kTraceStride + 6] = (unsigned long long)nat;
 }
 
 
 __device__ __forceinline__ int vload(const int* p) { return *((volatile const int*)p); }
+
+// Dynamic tile scheduling of one phase: blocks take the entries of the active tile list in order
+// from the phase's counter (one atomic per tile, the next index requested while the current tile
+// is processed), so a block that finishes early takes more tiles and every block reaches the
+// grid barrier at about the same time. Results do not depend on which block processes a tile
+// (partial sums are combined in tile order). Counter g % CTRL_NQ of phase g (three phases per
+// super-step) is zeroed by block 0 in phase g + 3, between two barriers on either side of its
+// uses; the host starts them at zero.
+template <typename F>
+__device__ __forceinline__ void for_tiles_dynamic(const KParams& P, int phase_g, int nat, const int* list, F f) {
+  __shared__ int s_a;
+  int* ctr = P.ctrl + CTRL_Q0 + phase_g % CTRL_NQ;
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl[CTRL_Q0 + (phase_g + 3) % CTRL_NQ] = 0;
+  if (threadIdx.x == 0) s_a = atomicAdd(ctr, 1);
+  __syncthreads();
+  int a = s_a;
+  while (a < nat) {
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(ctr, 1);
+    f(list[a]);
+    __syncthreads();
+    if (threadIdx.x == 0) s_a = next;
+    __syncthreads();
+    a = s_a;
+  }
+}
 
 // Arrival of this block's tile for system s; true (block-uniform) for the last arriver.
 __device__ __forceinline__ bool arrive_last(KState* S, int ntiles_s) {
@@ -272,45 +311,20 @@ __device__ __forceinline__ void tile_spmv(const cplx<T>* val, const uint8_t* cfl
   }
 }
 
+
+__device__ __forceinline__ cw cw_add(const cw& a, const cw& b) {
+  dacc2 acc;
+  acc.s = cw_hi(a);
+  acc.c = cw_lo(a);
+  acc.add(cw_hi(b), cw_lo(b));
+  float2 hi, lo;
+  acc.get(hi, lo);
+  return cw_from(hi, lo);
+}
+
 // L2 prefetch of one address (no register result, nothing waits for it)
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-// Double-word version of tile_spmv: first(row, q, complex_row_flag), fix(row, imaginary part).
-// With `pf` = d > 0, each thread prefetches the 27 matrix values of the row it will reach d
-// iterations later into L2 before working on the current one, so the streamed matrix is mostly
-// an L2 hit when it is loaded.
-template <typename F1, typename F2>
-__device__ __forceinline__ void tile_spmv_dw(const float2* valw, const uint8_t* cflag, const cw* x, int64_t n,
-                                             int64_t Nx, int64_t NxNy, int64_t row0, int64_t row1, F1 first,
-                                             F2 fix, int pf = 0) {
-  const float2* vim = valw + 27 * n;
-  int has_c = 0;
-  const int64_t ahead = (int64_t)pf * kBlock;
-  for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += kBlock) {
-    if (pf && r0 + ahead < row1)
-#pragma unroll
-      for (int k = 0; k < 27; ++k) prefetch_l2(valw + (int64_t)k * n + r0 + ahead);
-    const cw s0 = dia_row_re_dw(valw, x, n, Nx, NxNy, r0);
-    const int c0 = cflag[r0];
-    first(r0, s0, c0);
-    has_c |= c0;
-  }
-  if (__syncthreads_or(has_c)) {
-    for (int64_t row = row0 + threadIdx.x; row < row1; row += kBlock)
-      if (cflag[row]) fix(row, dia_row_im_dw(vim, x, n, Nx, NxNy, row));
-  }
-}
-
-__device__ __forceinline__ cw cw_add(const cw& a, const cw& b) {
-  dacc re(a.rh, a.rl), im(a.ih, a.il);
-  re.add(b.rh, b.rl);
-  im.add(b.ih, b.il);
-  cw out;
-  re.get(out.rh, out.rl);
-  im.get(out.ih, out.il);
-  return out;
 }
 
 // Inner stop of a refinement step: the inner estimate is relative to ||r_outer||; stop at the

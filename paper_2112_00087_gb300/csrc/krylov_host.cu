@@ -92,7 +92,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     const size_t n = sys[k].ctx->n, nnz = 27 * n;  // slot-major 27-point values
     bytes += rnd(nnz * sizeof(cd)) + rnd(n * sizeof(cd)) * 2 + rnd(n);  // val, b, r, row flags
     if (prec == 1) bytes += rnd(nnz * sizeof(cf)) + 4 * rnd(n * sizeof(cf));
-    if (prec == 2) bytes += rnd(nnz * 2 * sizeof(float2)) + 4 * rnd(n * sizeof(cw));
+    if (prec == 2) bytes += rnd(54 * (n + (n & 1)) * sizeof(float2)) + 4 * rnd(n * sizeof(cw));
     bytes += 2 * rnd(n * sizeof(cd));  // p, q (FP64 COCG, also the fallback of the mixed solver)
     if (!(bicg || tfq)) bytes += rnd(n * sizeof(cd));  // best iterate of FP64 COCG
     if (bicg || tfq) bytes += 3 * rnd(n * sizeof(cd));  // rs, s, t (TFQMR: r0*, w, A u)
@@ -102,7 +102,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   }
   const char* tenv = getenv("HELM_TRACE_STEPS");
   const int trace_steps = tenv ? std::max(0, std::min(atoi(tenv), 100000)) : 0;
-  bytes += rnd((size_t)trace_steps * 6 * sizeof(unsigned long long));
+  bytes += rnd((size_t)trace_steps * kTraceStride * sizeof(unsigned long long));
   bytes += rnd(nsys * sizeof(KSys)) + rnd(nsys * sizeof(KState)) + rnd(ntiles * sizeof(KTile)) +
            2 * rnd(ntiles * sizeof(int)) + rnd(CTRL_N * sizeof(int)) + rnd(2 * (size_t)ntiles * sizeof(cd)) +
            rnd(sizeof(GridBar));
@@ -132,7 +132,8 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     Y.x = sys[k].p_out;
     Y.r = A.take<cd>(c->n);
     if (prec == 2) {
-      Y.valw = A.take<float2>(54 * (size_t)c->n);
+      Y.nsw = c->n + (c->n & 1);  // even slot stride: every slot starts 16-byte aligned
+      Y.valw = A.take<float2>(54 * (size_t)Y.nsw);
       Y.xw = A.take<cw>(c->n);
       Y.rw = A.take<cw>(c->n);
       Y.pw = A.take<cw>(c->n);
@@ -178,7 +179,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
       st = jacobi_prepare(reinterpret_cast<double*>(val), cflag, Y.djac, c->n, c->mesh.nx, c->mesh.ny, c->mesh.nz, s);
     if (st == HELM_OK && prec == 1) st = cast_values(val, const_cast<cf*>(Y.val32), 27 * c->n, s);
     if (st == HELM_OK && prec == 2)
-      st = split_values(reinterpret_cast<const double*>(val), const_cast<float2*>(Y.valw), 54 * c->n, s);
+      st = split_values(reinterpret_cast<const double*>(val), const_cast<float2*>(Y.valw), c->n, Y.nsw, 54, s);
     if (st != HELM_OK) {
       cudaFree(A.base);
       return st;
@@ -194,7 +195,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   int* d_ctrl = A.take<int>(CTRL_N);
   cd* d_part = A.take<cd>(2 * (size_t)ntiles);
   GridBar* d_bar = A.take<GridBar>(1);
-  unsigned long long* d_trace = trace_steps ? A.take<unsigned long long>((size_t)trace_steps * 6) : nullptr;
+  unsigned long long* d_trace = trace_steps ? A.take<unsigned long long>((size_t)trace_steps * kTraceStride) : nullptr;
   std::vector<int> l0(ntiles);
   for (int t = 0; t < ntiles; ++t) l0[t] = t;
   int ctrl[CTRL_N] = {0};
@@ -230,8 +231,13 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   P.stall = o.stall_window;
   P.trace = d_trace;
   P.trace_steps = trace_steps;
-  const char* pfenv = getenv("HELM_PREFETCH");  // tuning knob: prefetch distance in block rows, 0 = off
+  // tuning knobs of the double-word solve: HELM_PREFETCH (per-thread L2 prefetch distance of the
+  // SpMV's matrix parts, block rows, 0 = off), HELM_PF_CHUNKS (bulk L2 prefetch distance of the
+  // vector phases, 256-row chunks, 0 = off)
+  const char* pfenv = getenv("HELM_PREFETCH");
+  const char* pcenv = getenv("HELM_PF_CHUNKS");
   P.prefetch = pfenv ? std::max(0, std::min(atoi(pfenv), 8)) : 1;
+  P.pf_chunks = pcenv ? std::max(0, std::min(atoi(pcenv), 16)) : 2;
 
   // Host-side fault injection for tests (never set in normal use): the barriers wait for one
   // block that does not exist and give up after 200 ms, so the launch ends with HELM_TIMEOUT
@@ -259,7 +265,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
   memset(&hb, 0, sizeof(hb));
   if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), d_st, nsys * sizeof(KState), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s);
-  std::vector<unsigned long long> htrace((size_t)trace_steps * 6);
+  std::vector<unsigned long long> htrace((size_t)trace_steps * kTraceStride);
   if (e == cudaSuccess && trace_steps)
     e = cudaMemcpyAsync(htrace.data(), d_trace, htrace.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -270,8 +276,8 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     double acc[6] = {0, 0, 0, 0, 0, 0};
     int cnt = 0;
     for (int k = 1; k < trace_steps; ++k) {
-      const unsigned long long* t = &htrace[(size_t)k * 6];
-      const unsigned long long prev = htrace[(size_t)(k - 1) * 6 + 5];
+      const unsigned long long* t = &htrace[(size_t)k * kTraceStride];
+      const unsigned long long prev = htrace[(size_t)(k - 1) * kTraceStride + 5];
       if (t[5] == 0 || prev == 0) break;
       acc[0] += (double)(t[0] - prev); acc[1] += (double)(t[1] - t[0]);
       acc[2] += (double)(t[2] - t[1]); acc[3] += (double)(t[3] - t[2]);
@@ -282,6 +288,20 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
       fprintf(stderr, "helm trace (%d steps, us): A work %.2f wait %.2f | B work %.2f wait %.2f | C work %.2f wait %.2f\n",
               cnt, acc[0] / cnt / 1e3, acc[1] / cnt / 1e3, acc[2] / cnt / 1e3, acc[3] / cnt / 1e3, acc[4] / cnt / 1e3,
               acc[5] / cnt / 1e3);
+    // raw per-step record (HELM_TRACE_FILE=path): step, the six phase times relative to the
+    // launch's first mark (ns), and the number of active tiles of the step
+    const char* tf = getenv("HELM_TRACE_FILE");
+    FILE* fh = tf ? fopen(tf, "w") : nullptr;
+    if (fh) {
+      const unsigned long long t0 = htrace[0];
+      for (int k = 0; k < trace_steps; ++k) {
+        const unsigned long long* t = &htrace[(size_t)k * kTraceStride];
+        if (t[5] == 0) break;
+        fprintf(fh, "%d %llu %llu %llu %llu %llu %llu %llu\n", k, t[0] - t0, t[1] - t0, t[2] - t0, t[3] - t0,
+                t[4] - t0, t[5] - t0, t[6]);
+      }
+      fclose(fh);
+    }
   }
   if (e == cudaSuccess) {
     float t_asm = 0.f, t_solve = 0.f;
