@@ -176,6 +176,9 @@ __device__ __forceinline__ cplx<T> dia_row_im(const T* __restrict__ vim, const c
 // Double-word i Im(a) x part of a row flagged complex (imaginary matrix parts as (hi, lo) float
 // pairs, slot-major with slot stride ns >= n): re -= Im(a) x.im, im += Im(a) x.re, Dot2-style
 // accumulation on the FP32 pipe, both components in one packed accumulator.
+// CLAMP: gather indices clamped into [0, n) (needed for rows within one stencil reach of
+// either end).
+template <bool CLAMP>
 __device__ __forceinline__ cw dia_row_im_dw2(const float2* __restrict__ vim, const cw* x, int64_t n, int64_t ns,
                                              int64_t Nx, int64_t NxNy, int64_t row) {
   dacc2 acc;
@@ -183,7 +186,7 @@ __device__ __forceinline__ cw dia_row_im_dw2(const float2* __restrict__ vim, con
   for (int k = 0; k < 27; ++k) {
     const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dl = k / 9 - 1;
     int64_t c = row + di + Nx * dj + NxNy * dl;
-    c = c < 0 ? 0 : (c >= n ? n - 1 : c);
+    if (CLAMP) c = c < 0 ? 0 : (c >= n ? n - 1 : c);
     const float2 b = vim[(int64_t)k * ns + row];
     const cw xv = x[c];
     acc.mac(make_float2(-b.x, b.x), make_float2(-b.y, b.y), make_float2(xv.ih, xv.rh), make_float2(xv.il, xv.rl));

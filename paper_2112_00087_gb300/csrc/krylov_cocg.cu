@@ -561,8 +561,8 @@ __device__ void phaseC_mixed(const KParams& P, int t, double* sh) {
 
 // Real-part product of one row in double-word arithmetic: matrix parts (slot stride ns) and x
 // by cached loads, three accumulators per component (one per stencil line dj), planes in order.
-// CLAMP: gather indices clamped into [0, n) (rows whose stencil reaches outside the index range;
-// the entries there are zero); interior rows skip the clamps.
+// CLAMP: gather indices clamped into [0, n) (rows within one stencil reach of either end; the
+// entries there are zero); interior rows skip the clamps.
 template <bool CLAMP>
 __device__ __forceinline__ cw dia_row_re_dw2(const float2* __restrict__ vre, const cw* x, int64_t n, int64_t ns,
                                              int64_t Nx, int64_t NxNy, int64_t row) {
@@ -615,7 +615,7 @@ __device__ __forceinline__ void tile_spmv_dw(const KSys& Y, const cw* x, int64_t
   if (__syncthreads_or(has_c)) {
     const float2* vim = Y.valw + 27 * ns;
     for (int64_t row = row0 + threadIdx.x; row < row1; row += kBlock)
-      if (Y.cflag[row]) fix(row, dia_row_im_dw2(vim, x, n, ns, Nx, NxNy, row));
+      if (Y.cflag[row]) fix(row, dia_row_im_dw2<true>(vim, x, n, ns, Nx, NxNy, row));
   }
 }
 

@@ -161,26 +161,29 @@ __device__ __forceinline__ void trace_count(const KParams& P, int step, int nat)
 __device__ __forceinline__ int vload(const int* p) { return *((volatile const int*)p); }
 
 // Dynamic tile scheduling of one phase: blocks take the entries of the active tile list in order
-// from the phase's counter (one atomic per tile, the next index requested while the current tile
-// is processed), so a block that finishes early takes more tiles and every block reaches the
-// grid barrier at about the same time. Results do not depend on which block processes a tile
-// (partial sums are combined in tile order). Counter g % CTRL_NQ of phase g (three phases per
-// super-step) is zeroed by block 0 in phase g + 3, between two barriers on either side of its
-// uses; the host starts them at zero.
+// from the phase's counter, one atomic per tile, so a block that finishes early takes more tiles
+// and every block reaches the grid barrier at about the same time. While the list holds more
+// than two tiles per block the next entry is requested as the current tile starts (hiding the
+// atomic's latency); with fewer it is requested after the tile, so no block holds a tile that an
+// idle block could have taken. Results do not depend on which block processes a tile (partial
+// sums are combined in tile order). Counter g % CTRL_NQ of phase g (three phases per super-step)
+// is zeroed by block 0 in phase g + 3, between two barriers on either side of its uses; the host
+// starts them at zero.
 template <typename F>
 __device__ __forceinline__ void for_tiles_dynamic(const KParams& P, int phase_g, int nat, const int* list, F f) {
   __shared__ int s_a;
   int* ctr = P.ctrl + CTRL_Q0 + phase_g % CTRL_NQ;
+  const bool ahead = nat > 2 * (int)gridDim.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl[CTRL_Q0 + (phase_g + 3) % CTRL_NQ] = 0;
   if (threadIdx.x == 0) s_a = atomicAdd(ctr, 1);
   __syncthreads();
   int a = s_a;
   while (a < nat) {
     int next = 0;
-    if (threadIdx.x == 0) next = atomicAdd(ctr, 1);
+    if (ahead && threadIdx.x == 0) next = atomicAdd(ctr, 1);
     f(list[a]);
     __syncthreads();
-    if (threadIdx.x == 0) s_a = next;
+    if (threadIdx.x == 0) s_a = ahead ? next : atomicAdd(ctr, 1);
     __syncthreads();
     a = s_a;
   }

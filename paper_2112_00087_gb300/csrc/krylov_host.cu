@@ -168,7 +168,7 @@ helm_status solve_cocg_batch(const BatchSystem* sys, int nsys, const helm_solve_
     }
     Y.tile0 = tile0[k];
     Y.ntiles = ntl[k];
-    st = assemble_values(c, sys[k].freq, val, b, s, true, /*dia=*/true, cflag);
+    if (st == HELM_OK) st = assemble_values(c, sys[k].freq, val, b, s, true, /*dia=*/true, cflag);
     if (st == HELM_OK && sys[k].rhs) {
       cudaError_t ce = cudaMemcpyAsync(b, sys[k].rhs, c->n * sizeof(cd), cudaMemcpyDeviceToDevice, s);
       if (ce != cudaSuccess) st = cuda_error(ce, "rhs copy");
