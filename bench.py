@@ -99,8 +99,6 @@ def cocg_fp64_bytes(n, nnz, st):
 # FP64 flops per row of one FP64 COCG step: 27 complex-by-real stencil products (4 flops each),
 # the p^T q and r^T r / ||r||^2 dot products, the x, r and p updates -- 152 in total.
 FP64_FLOPS_PER_ROW_STEP = 27 * 4 + 8 + 8 + 8 + 8 + 4 + 8
-# GB300 FP64: 2 FMA per SM per clock x 152 SMs x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25).
-FP64_PEAK_TFLOPS = 1.25
 
 
 def cocg_fp64_flops(n, st):
@@ -298,8 +296,11 @@ def timed(fn, torch, K, W, dist=None):
     return e0.elapsed_time(e1) / 1000.0, wall, outs
 
 
-def spmv_roofline(helm, torch, peak_gbs):
-    """helm_spmv on the 2,203,161-node lattice, complex128 and complex64, L2 flushed between reps."""
+def spmv_roofline(helm, torch, peak_gbs, fp64_tflops=None):
+    """helm_spmv on the 2,203,161-node lattice, complex128 and complex64, L2 flushed between reps.
+    The complex128 products are bound by the FP64 pipe: for them the line also gives the FP64 rate
+    (4 flops per stored entry: the real part of each entry times x's two components) against the
+    measured FP64 peak."""
     pr = hi.cabin_problem(200, 112, 96)
     m = pr.mesh
     ctx = helm.Context(m.nx, m.ny, m.nz, m.Lx, m.Ly, m.Lz)
@@ -333,6 +334,10 @@ def spmv_roofline(helm, torch, peak_gbs):
         best, med = min(times), statistics.median(times)
         out[name] = {"n": ctx.n, "nnz": ctx.nnz, "bytes": b, "best_ms": best * 1e3, "median_ms": med * 1e3,
                      "gbs_best": b / best / 1e9, "gbs_median": b / med / 1e9, "frac_median": b / med / 1e9 / peak_gbs}
+        if vb == 16 and fp64_tflops:
+            fl = 4.0 * (ctx.nnz if fmt == helm.HELM_FMT_CSR else 27 * ctx.n)
+            out[name]["fp64_tflops_median"] = fl / med / 1e12
+            out[name]["fp64_frac_median"] = fl / med / 1e12 / fp64_tflops
         A.free()
     ctx.close()
     return out
@@ -478,6 +483,10 @@ def run_gpu(args):
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     peaks, peak_kind = measured_peaks()
     peak_gbs = float(peaks["hbm_gbs"])
+    # FP64 FMA rate of this GPU, measured by the library's probe kernel (CUDA events): the
+    # roofline of the FP64-bound kernels
+    fp64_fma = helm.helm_probe_fp64_fma(20000)
+    fp64_tflops = 2.0 * fp64_fma / 1e12
 
     freqs, probs, ctxs, outs = build_sweep(args.nfreq, helm, torch, args.workload)
     nsys = len(ctxs)
@@ -536,10 +545,10 @@ def run_gpu(args):
         # the FP64 step is bound by the FP64 pipe on GB300: report that roofline, HBM beside it
         fl = sum(flops_fn(c.n, s) for c, s in zip(ctxs, stats))
         tf = fl / kern_s / 1e12
-        roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+        roof = {"bound": "alu", "achieved": tf, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": tf / fp64_tflops, "traffic": traffic,
                 "kernel": kname, "algorithmic_flops": fl, "kernel_ms": prof["solve_ms"],
-                "peak_kind": "derived: FP64 2 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "peak_kind": "measured: FP64 FMA probe kernel (helm_probe_fp64_fma), 2 flops per FMA",
                 "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "algorithmic_bytes", "peak_kind")}}
     desc = ("sweep256: %d log-spaced frequencies 20-500 Hz, each on its own wavelength-scaled 2.5x1.4x1.2 m "
             "cabin lattice (24x14x12..148x83x71, %d nodes total), sun-roof Dirichlet pressure + random seat "
@@ -561,6 +570,9 @@ def run_gpu(args):
                           "relres_max": max(s["relres"] for s in stats)},
            "phases_ms": {"assemble": prof["assemble_ms"], "solve": prof["solve_ms"]},
            "roofline": roof,
+           "fp64_peak": {"fma_per_s": fp64_fma, "tflops": fp64_tflops,
+                         "how": "helm_probe_fp64_fma: 8 independent FMA chains per thread, 16 blocks of 256 per SM, "
+                                "CUDA events"},
            "gpu_launches": int(launches), "clocks": clk}
 
     if rank == 0 and not args.quick:
@@ -596,7 +608,7 @@ def run_gpu(args):
                            if leg_ is not None}
         if "fp64_sequential" in out:
             out["speedups"]["vs_fp64_same_preconditioner_sequential"] = value / out["fp64_sequential"]["freqs_per_s"]
-        out["spmv"] = spmv_roofline(helm, torch, peak_gbs)
+        out["spmv"] = spmv_roofline(helm, torch, peak_gbs, fp64_tflops)
 
         # end to end through host buffers: boundary data in from pinned memory, pressures out
         hb = [(torch.from_numpy(p.beta).pin_memory(), torch.from_numpy(p.dir_nodes).pin_memory(),
@@ -660,93 +672,143 @@ def run_configs(args):
         return p, st, dt, pr_
 
     res = {}
-    # box100: GMRES(30) and COCG, FP64, 100 Hz
-    c = ctx_of(hi.small_box_problem())
-    out = {}
-    for name, o in (("gmres30", helm.make_opts("gmres", restart=30, tol=TOL, maxit=20000)),
-                    ("cocg", helm.make_opts("cocg", tol=TOL, maxit=20000)),
-                    ("bicgstab", helm.make_opts("bicgstab", tol=TOL, maxit=20000))):
-        run(c, [100.0], o)
-        _, st, dt, pr_ = run(c, [100.0], o)
-        out[name] = {"ms": dt * 1e3, "solve_ms": pr_["solve_ms"], "iterations": st[0]["iterations"],
-                     "restarts": st[0]["restarts"], "relres": st[0]["relres"], "status": st[0]["status"]}
-    res["box100"] = out
-    # cabin282k: GMRES(50) + RAS 8x4x4 overlap 2 at 20/100/200 Hz, and COCG for comparison
-    c = ctx_of(hi.cabin_problem(100, 56, 48))
-    out = {}
-    for f in (20.0, 100.0, 200.0):
+    names = args.configs or ["box100", "cabin282k", "cabin2m", "adjoint64", "resonance64", "spmm"]
+    want = lambda name: name in names  # noqa: E731
+    if want("box100"):
+        # box100: GMRES(30) and COCG, FP64, 100 Hz
+        c = ctx_of(hi.small_box_problem())
+        out = {}
+        for name, o in (("gmres30", helm.make_opts("gmres", restart=30, tol=TOL, maxit=20000)),
+                        ("cocg", helm.make_opts("cocg", tol=TOL, maxit=20000)),
+                        ("bicgstab", helm.make_opts("bicgstab", tol=TOL, maxit=20000))):
+            run(c, [100.0], o)
+            _, st, dt, pr_ = run(c, [100.0], o)
+            out[name] = {"ms": dt * 1e3, "solve_ms": pr_["solve_ms"], "iterations": st[0]["iterations"],
+                         "restarts": st[0]["restarts"], "relres": st[0]["relres"], "status": st[0]["status"]}
+        res["box100"] = out
+    if want("cabin282k"):
+        # cabin282k: GMRES(50) + RAS 8x4x4 overlap 2 at 20/100/200 Hz, and COCG for comparison
+        c = ctx_of(hi.cabin_problem(100, 56, 48))
+        out = {}
+        for f in (20.0, 100.0, 200.0):
+            o = helm.make_opts("gmres", restart=50, tol=TOL, maxit=5000, precond="ras", ras_parts=(8, 4, 4), ras_overlap=2)
+            _, st, dt, pr_ = run(c, [f], o)
+            o2 = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
+            _, st2, dt2, pr2 = run(c, [f], o2)
+            _, st3, dt3, _ = run(c, [f], helm.make_opts("bicgstab", tol=TOL, maxit=40000))
+            o4 = helm.make_opts("gmres", restart=50, tol=TOL, maxit=5000, precond="oras", ras_parts=(8, 4, 4), ras_overlap=2)
+            _, st4, dt4, pr4 = run(c, [f], o4)
+            out["%g" % f] = {"ras_gmres50": {"ms_total": dt * 1e3, "solve_ms": pr_["solve_ms"],
+                                             "iterations": st[0]["iterations"], "relres": st[0]["relres"],
+                                             "status": st[0]["status"]},
+                             "cocg": {"ms_total": dt2 * 1e3, "iterations": st2[0]["iterations"],
+                                      "relres": st2[0]["relres"], "status": st2[0]["status"]},
+                             "bicgstab": {"ms_total": dt3 * 1e3, "iterations": st3[0]["iterations"],
+                                          "relres": st3[0]["relres"], "status": st3[0]["status"]},
+                             "oras_gmres50": {"ms_total": dt4 * 1e3, "solve_ms": pr4["solve_ms"],
+                                              "iterations": st4[0]["iterations"], "relres": st4[0]["relres"],
+                                              "status": st4[0]["status"]}}
+        res["cabin282k"] = out
+    if want("cabin2m"):
+        # cabin2m: every 8th of the 32 frequencies, FP64 vs mixed, batched per precision
+        pr = hi.cabin_problem(200, 112, 96)
+        c = ctx_of(pr)
+        fr = list(np.geomspace(100.0, 400.0, 32)[::8])
+        p64, st64, dt64, _ = run(c, fr, helm.make_opts("cocg", tol=TOL, maxit=60000, stall_window=STALL))
+        pmx, stmx, dtmx, _ = run(c, fr, mixed_opts(helm, 60000))
+        pdw, stdw, dtdw, _ = run(c, fr, dw_opts(helm, 60000, "jacobi"))
+        err_dw = [float((torch.linalg.norm(pdw[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
+        err = [float((torch.linalg.norm(pmx[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
+        res["cabin2m_sample"] = {"freqs": [float(f) for f in fr], "n": c.n,
+                                 "fp64": {"freqs_per_s": len(fr) / dt64, "iterations": [s_["iterations"] for s_ in st64],
+                                          "status": [s_["status"] for s_ in st64]},
+                                 "mixed": {"freqs_per_s": len(fr) / dtmx, "iterations": [s_["iterations"] for s_ in stmx],
+                                           "c64": [s_["iterations_c64"] for s_ in stmx], "outer": [s_["outer"] for s_ in stmx],
+                                           "status": [s_["status"] for s_ in stmx]},
+                                 "rel_l2_mixed_vs_fp64": err,
+                                 "dw_jacobi": {"freqs_per_s": len(fr) / dtdw, "iterations": [s_["iterations"] for s_ in stdw],
+                                               "status": [s_["status"] for s_ in stdw], "rel_l2_vs_fp64": err_dw}}
+        del p64, pmx, pdw
+    if want("ras282k"):
+        # one GMRES(50) + RAS 8x4x4 (overlap 2) solve of the 282k cabin at 100 Hz (profiling case)
+        c = ctx_of(hi.cabin_problem(100, 56, 48))
         o = helm.make_opts("gmres", restart=50, tol=TOL, maxit=5000, precond="ras", ras_parts=(8, 4, 4), ras_overlap=2)
-        _, st, dt, pr_ = run(c, [f], o)
-        o2 = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
-        _, st2, dt2, pr2 = run(c, [f], o2)
-        _, st3, dt3, _ = run(c, [f], helm.make_opts("bicgstab", tol=TOL, maxit=40000))
-        o4 = helm.make_opts("gmres", restart=50, tol=TOL, maxit=5000, precond="oras", ras_parts=(8, 4, 4), ras_overlap=2)
-        _, st4, dt4, pr4 = run(c, [f], o4)
-        out["%g" % f] = {"ras_gmres50": {"ms_total": dt * 1e3, "solve_ms": pr_["solve_ms"],
-                                         "iterations": st[0]["iterations"], "relres": st[0]["relres"],
-                                         "status": st[0]["status"]},
-                         "cocg": {"ms_total": dt2 * 1e3, "iterations": st2[0]["iterations"],
-                                  "relres": st2[0]["relres"], "status": st2[0]["status"]},
-                         "bicgstab": {"ms_total": dt3 * 1e3, "iterations": st3[0]["iterations"],
-                                      "relres": st3[0]["relres"], "status": st3[0]["status"]},
-                         "oras_gmres50": {"ms_total": dt4 * 1e3, "solve_ms": pr4["solve_ms"],
-                                          "iterations": st4[0]["iterations"], "relres": st4[0]["relres"],
-                                          "status": st4[0]["status"]}}
-    res["cabin282k"] = out
-    # cabin2m: every 8th of the 32 frequencies, FP64 vs mixed, batched per precision
-    pr = hi.cabin_problem(200, 112, 96)
-    c = ctx_of(pr)
-    fr = list(np.geomspace(100.0, 400.0, 32)[::8])
-    p64, st64, dt64, _ = run(c, fr, helm.make_opts("cocg", tol=TOL, maxit=60000, stall_window=STALL))
-    pmx, stmx, dtmx, _ = run(c, fr, mixed_opts(helm, 60000))
-    pdw, stdw, dtdw, _ = run(c, fr, dw_opts(helm, 60000, "jacobi"))
-    err_dw = [float((torch.linalg.norm(pdw[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
-    err = [float((torch.linalg.norm(pmx[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
-    res["cabin2m_sample"] = {"freqs": [float(f) for f in fr], "n": c.n,
-                             "fp64": {"freqs_per_s": len(fr) / dt64, "iterations": [s_["iterations"] for s_ in st64],
-                                      "status": [s_["status"] for s_ in st64]},
-                             "mixed": {"freqs_per_s": len(fr) / dtmx, "iterations": [s_["iterations"] for s_ in stmx],
-                                       "c64": [s_["iterations_c64"] for s_ in stmx], "outer": [s_["outer"] for s_ in stmx],
-                                       "status": [s_["status"] for s_ in stmx]},
-                             "rel_l2_mixed_vs_fp64": err,
-                             "dw_jacobi": {"freqs_per_s": len(fr) / dtdw, "iterations": [s_["iterations"] for s_ in stdw],
-                                           "status": [s_["status"] for s_ in stdw], "rel_l2_vs_fp64": err_dw}}
-    del p64, pmx, pdw
-    # adjoint64: 64 frequencies 20-300 Hz on the 282k cabin, forward + adjoint
-    pr = hi.cabin_problem(100, 56, 48)
-    c = ctx_of(pr)
-    fr = list(np.geomspace(20.0, 300.0, 64))
-    o = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
-    p, st, dtf, _ = run(c, fr, o)
-    w = torch.from_numpy(hi.listener_weights(pr.mesh)).cuda()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    J, gb, gd = helm.helm_adjoint_grad(c, fr, o, p, w)
-    torch.cuda.synchronize()
-    dta = time.perf_counter() - t0
-    res["adjoint64"] = {"forward_s": dtf, "adjoint_s": dta, "ms_per_frequency_forward_plus_adjoint": (dtf + dta) / 64 * 1e3,
-                        "J": J, "converged_forward": sum(1 for s_ in st if s_["status"] == 0),
-                        "grad_beta_norm": float(torch.linalg.norm(gb).item()), "n_seat_faces": int((torch.from_numpy(pr.beta) != 0).sum())}
-    # resonance64: 64 FFT bins 2-33.5 Hz on the 282k cabin, sun-roof pressure shaped by the
-    # synthetic PSD (the solve is linear in the Dirichlet data, so each solution is the unit-pattern
-    # solution times the bin's complex amplitude); FP64 COCG and the double-word mode, batched
-    pr = hi.cabin_problem(100, 56, 48)
-    c = ctx_of(pr)
-    fr = [float(f) for f in hi.resonance_freqs(64)]
-    amp = torch.from_numpy(hi.resonance_spectrum(np.array(fr))).cuda()
-    w = torch.from_numpy(hi.listener_weights(pr.mesh)).cuda()
-    out = {"n": c.n, "freqs": [fr[0], fr[-1], len(fr)]}
-    for name, o in (("fp64", fp64_opts(helm, 40000)), ("dw", dw_opts(helm, 40000)),
-                    ("dw_jacobi", dw_opts(helm, 40000, "jacobi"))):
-        run(c, fr, o)
-        p, st, dt, _ = run(c, fr, o)
-        level = [float((abs(amp[k]) ** 2 * (w * (p[k].abs() ** 2)).sum()).item()) for k in range(len(fr))]
-        out[name] = {"freqs_per_s": len(fr) / dt, "iterations": int(sum(s_["iterations"] for s_ in st)),
-                     "converged": sum(1 for s_ in st if s_["status"] == 0),
-                     "listener_peak_hz": fr[int(np.argmax(level))]}
-    res["resonance64"] = out
-    peaks, _ = measured_peaks()
-    res["spmm_cabin2m"] = spmm_multi_roofline(helm, torch, float(peaks["hbm_gbs"]))
+        _, st, dt, pr_ = run(c, [100.0], o)
+        res["ras282k"] = {"ms_total": dt * 1e3, "solve_ms": pr_["solve_ms"], "iterations": st[0]["iterations"],
+                          "relres": st[0]["relres"], "status": st[0]["status"]}
+    if want("cabin2m32"):
+        # all 32 frequencies geomspace(100, 400, 32) on the 2,203,161-node cabin: FP64 COCG and the
+        # benchmark's main mode, batched per mode; the main mode's error against the FP64 results
+        pr = hi.cabin_problem(200, 112, 96)
+        c = ctx_of(pr)
+        fr = list(np.geomspace(100.0, 400.0, 32))
+        out = {"n": c.n, "freqs": [fr[0], fr[-1], len(fr)]}
+        p64, st64, dt64, _ = run(c, fr, helm.make_opts("cocg", tol=TOL, maxit=60000, stall_window=STALL))
+        out["fp64"] = {"freqs_per_s": len(fr) / dt64, "iterations": [s_["iterations"] for s_ in st64],
+                       "converged": sum(1 for s_ in st64 if s_["status"] == 0),
+                       "relres_max": max(s_["relres"] for s_ in st64)}
+        pdw, stdw, dtdw, _ = run(c, fr, dw_opts(helm, 60000, "jacobi"))
+        err = [float((torch.linalg.norm(pdw[k] - p64[k]) / torch.linalg.norm(p64[k])).item()) for k in range(len(fr))]
+        out["main_mode"] = {"freqs_per_s": len(fr) / dtdw, "iterations": [s_["iterations"] for s_ in stdw],
+                            "converged": sum(1 for s_ in stdw if s_["status"] == 0),
+                            "relres_max": max(s_["relres"] for s_ in stdw),
+                            "rel_l2_vs_fp64": err, "rel_l2_vs_fp64_max": max(err)}
+        out["speedup_main_vs_fp64"] = dt64 / dtdw
+        res["cabin2m32"] = out
+        del p64, pdw
+    if want("adjoint64"):
+        # adjoint64: 64 frequencies 20-300 Hz on the 282k cabin, forward + adjoint
+        pr = hi.cabin_problem(100, 56, 48)
+        c = ctx_of(pr)
+        fr = list(np.geomspace(20.0, 300.0, 64))
+        o = helm.make_opts("cocg", tol=TOL, maxit=40000, stall_window=STALL)
+        p, st, dtf, _ = run(c, fr, o)
+        w = torch.from_numpy(hi.listener_weights(pr.mesh)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, gb, gd = helm.helm_adjoint_grad(c, fr, o, p, w)
+        torch.cuda.synchronize()
+        dta = time.perf_counter() - t0
+        # the same gradient through the benchmark's main mode (double-word inner COCG, FP64
+        # refinement, symmetric Jacobi) for forward and adjoint solves, against the FP64 one
+        od = dw_opts(helm, 40000, "jacobi")
+        p2, st2, dtf2, _ = run(c, fr, od)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J2, gb2, gd2 = helm.helm_adjoint_grad(c, fr, od, p2, w)
+        torch.cuda.synchronize()
+        dta2 = time.perf_counter() - t0
+        res["adjoint64"] = {"forward_s": dtf, "adjoint_s": dta, "ms_per_frequency_forward_plus_adjoint": (dtf + dta) / 64 * 1e3,
+                            "J": J, "converged_forward": sum(1 for s_ in st if s_["status"] == 0),
+                            "grad_beta_norm": float(torch.linalg.norm(gb).item()), "n_seat_faces": int((torch.from_numpy(pr.beta) != 0).sum()),
+                            "main_mode": {"forward_s": dtf2, "adjoint_s": dta2,
+                                          "ms_per_frequency_forward_plus_adjoint": (dtf2 + dta2) / 64 * 1e3,
+                                          "J_rel_diff_vs_fp64": abs(J2 - J) / abs(J),
+                                          "grad_beta_rel_l2_vs_fp64": float((torch.linalg.norm(gb2 - gb) / torch.linalg.norm(gb)).item()),
+                                          "grad_pdir_rel_l2_vs_fp64": float((torch.linalg.norm(gd2 - gd) / torch.linalg.norm(gd)).item()),
+                                          "converged_forward": sum(1 for s_ in st2 if s_["status"] == 0)}}
+    if want("resonance64"):
+        # resonance64: 64 FFT bins 2-33.5 Hz on the 282k cabin, sun-roof pressure shaped by the
+        # synthetic PSD (the solve is linear in the Dirichlet data, so each solution is the unit-pattern
+        # solution times the bin's complex amplitude); FP64 COCG and the double-word mode, batched
+        pr = hi.cabin_problem(100, 56, 48)
+        c = ctx_of(pr)
+        fr = [float(f) for f in hi.resonance_freqs(64)]
+        amp = torch.from_numpy(hi.resonance_spectrum(np.array(fr))).cuda()
+        w = torch.from_numpy(hi.listener_weights(pr.mesh)).cuda()
+        out = {"n": c.n, "freqs": [fr[0], fr[-1], len(fr)]}
+        for name, o in (("fp64", fp64_opts(helm, 40000)), ("dw", dw_opts(helm, 40000)),
+                        ("dw_jacobi", dw_opts(helm, 40000, "jacobi"))):
+            run(c, fr, o)
+            p, st, dt, _ = run(c, fr, o)
+            level = [float((abs(amp[k]) ** 2 * (w * (p[k].abs() ** 2)).sum()).item()) for k in range(len(fr))]
+            out[name] = {"freqs_per_s": len(fr) / dt, "iterations": int(sum(s_["iterations"] for s_ in st)),
+                         "converged": sum(1 for s_ in st if s_["status"] == 0),
+                         "listener_peak_hz": fr[int(np.argmax(level))]}
+        res["resonance64"] = out
+    if want("spmm"):
+        peaks, _ = measured_peaks()
+        res["spmm_cabin2m"] = spmm_multi_roofline(helm, torch, float(peaks["hbm_gbs"]))
     print(json.dumps({"configs": res}), flush=True)
 
 
@@ -811,7 +873,9 @@ def main():
     ap.add_argument("--precond", default="jacobi", choices=["none", "jacobi"],
                     help="Jacobi preconditioning (symmetric for COCG, right for BiCGSTAB / TFQMR)")
     ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
-    ap.add_argument("--configs", action="store_true", help="measure the secondary workloads instead")
+    ap.add_argument("--configs", nargs="*", default=None,
+                    help="measure the secondary workloads instead (all, or the named ones: box100 cabin282k "
+                         "ras282k cabin2m cabin2m32 adjoint64 resonance64 spmm)")
     ap.add_argument("--autotune", action="store_true",
                     help="search the persistent engine's launch-shape knobs on this workload (one line of JSON)")
     ap.add_argument("--traffic", type=float, default=None,
@@ -821,7 +885,7 @@ def main():
         run_reference(args)
     elif args.autotune:
         run_autotune(args)
-    elif args.configs:
+    elif args.configs is not None:
         run_configs(args)
     else:
         run_gpu(args)

@@ -274,6 +274,14 @@ helm_status helm_adjoint_grad(helm_ctx* ctx, const double* freqs_hz, int32_t nfr
 /* Timing record of the calling thread's last helm_solve / helm_solve_batch (host, written). */
 helm_status helm_last_profile(helm_profile* out);
 
+/* Measurement aid (no counterpart in the paper's method; it calibrates the rooflines of the
+ * complex double-precision kernels of paper Sec. 4, whose FP64 multiply-adds bound them on GPUs
+ * with a reduced FP64 rate): runs a kernel of independent FP64 FMA chains over the whole device
+ * for `iters` steps per chain on `stream` (NULL = default stream), times it with CUDA events and
+ * writes the measured rate in FMA/s to *fma_per_s (host). Allocates and frees a small device
+ * buffer; synchronises the stream. HELM_ERR_ARG for iters <= 0 or a null output. */
+helm_status helm_probe_fp64_fma(int32_t iters, double* fma_per_s, void* stream);
+
 /* Adjoint gradient for any real loss L(p) of the pressures (the backward step of an autograd
  * wrapper). grad_p (dev, complex128 [nfreq][n]) is PyTorch's gradient of L with respect to
  * p = helm_solve's output (dL/dRe p + i dL/dIm p). With lam = A^-1 conj(grad_p) (one adjoint

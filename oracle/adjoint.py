@@ -11,7 +11,9 @@ adjoint system A_red lam = W conj(p). Zero lam on the Dirichlet nodes to get lam
   per Dirichlet node:    mu = W_D conj(p_D) - A_DF lam_F,     grad_p_D    =  2 conj(mu)
 
 with B_e the quad mass of face e and A_DF taken from the matrix before elimination; both
-summed over frequencies. Solves use scipy's sparse LU.
+summed over frequencies. Solves use scipy's sparse LU, or with ``dense=True`` a dense LU of the
+full matrix (LAPACK getrf/getrs through scipy.linalg) -- the plain definition of the solve, for
+lattices small enough to hold A densely (config 0's 4,641 nodes: 344 MB).
 
 Pinned (tests/test_oracle_adjoint.py): central finite differences of J (perturbing real and
 imaginary parts separately) on random faces and Dirichlet nodes.
@@ -22,7 +24,7 @@ import scipy.sparse.linalg as spl
 from . import fem, mesh as _mesh
 
 
-def objective_and_gradient(prob, freqs, w, KM=None):
+def objective_and_gradient(prob, freqs, w, KM=None, dense=False):
     """Returns (J, grad_beta [n_bfaces] complex, grad_pdir [n_dir] complex, list of p)."""
     m = prob.mesh
     KM = KM if KM is not None else fem.assemble_KM(m)
@@ -37,11 +39,17 @@ def objective_and_gradient(prob, freqs, w, KM=None):
     for f in freqs:
         A = fem.helmholtz_matrix(prob, f, KM)
         A_red, b = fem.eliminate_dirichlet(A, prob.dir_nodes, prob.p_dir)
-        lu = spl.splu(A_red.tocsc())
-        p = lu.solve(b)
+        if dense:
+            import scipy.linalg as sla
+            lu = sla.lu_factor(A_red.toarray())
+            solve = lambda v: sla.lu_solve(lu, v)  # noqa: E731
+        else:
+            lu = spl.splu(A_red.tocsc())
+            solve = lu.solve
+        p = solve(b)
         ps.append(p)
         J += float(np.sum(w * np.abs(p) ** 2))
-        lam = lu.solve(w * np.conj(p))
+        lam = solve(w * np.conj(p))
         lamF = np.where(isD, 0.0, lam)
         k = fem.wavenumber(f, prob.c)
         for e, (nodes, (hu, hv)) in enumerate(quads):

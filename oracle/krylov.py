@@ -507,3 +507,99 @@ def cocg_ir(matvec, b, tol=1e-10, inner_tol=1e-12, inner_maxit=100000, max_outer
         st.history += [h * rel for h in hist]
         if est < 1.0:
             x = x + rn * d
+
+
+def gmres_inner_c64(matvec32, s, m, target, maxit_left):
+    """Inner solve of the complex64 GMRES-IR form: restarted GMRES(m) on A d = s with the
+    Arnoldi basis and the products with A in complex64 (``matvec32``: a complex64 matrix times a
+    complex64 vector, FP32 accumulation), the Gram-Schmidt inner products and norms accumulated
+    in FP64 from the complex64 values (CGS2), the Givens rotations and the least-squares solve
+    in FP64 (Saad 2nd ed. Sec. 6.5, the rotations of ``gmres``), the correction d accumulated in
+    FP64. Each restart begins from the inner residual s - A d evaluated in complex64. Stops when
+    the Givens estimate |g_{j+1}| / ||s|| reaches `target` or after `maxit_left` steps.
+    Returns (d, steps, final estimate, breakdown, estimate history)."""
+    s = np.asarray(s, dtype=np.complex128)
+    n = s.shape[0]
+    ns = np.linalg.norm(s)
+    d = np.zeros(n, dtype=np.complex128)
+    r = s.astype(np.complex64)
+    k, est, hist = 0, 1.0, []
+    while True:
+        beta0 = np.linalg.norm(r.astype(np.complex128))
+        if beta0 == 0:
+            return d, k, 0.0, False, hist
+        V = np.zeros((m + 1, n), dtype=np.complex64)
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta0
+        V[0] = (r.astype(np.complex128) / beta0).astype(np.complex64)
+        j_end, bd = 0, False
+        for j in range(m):
+            w = matvec32(V[j]).astype(np.complex128)
+            k += 1
+            Vj = V[: j + 1].astype(np.complex128)
+            h = Vj.conj() @ w
+            w = w - Vj.T @ h
+            h2 = Vj.conj() @ w
+            w = w - Vj.T @ h2
+            h = h + h2
+            w32 = w.astype(np.complex64)
+            hn = np.linalg.norm(w32.astype(np.complex128))
+            H[: j + 1, j] = h
+            H[j + 1, j] = hn
+            for i in range(j):
+                H[i, j], H[i + 1, j] = _rotate(cs[i], sn[i], H[i, j], H[i + 1, j])
+            cs[j], sn[j] = givens(H[j, j], H[j + 1, j])
+            H[j, j], H[j + 1, j] = _rotate(cs[j], sn[j], H[j, j], H[j + 1, j])
+            g[j], g[j + 1] = _rotate(cs[j], sn[j], g[j], 0.0)
+            est = abs(g[j + 1]) / ns
+            hist.append(est)
+            j_end = j + 1
+            bd = hn == 0
+            if est <= target or bd or k >= maxit_left:
+                break
+            V[j + 1] = (w32.astype(np.complex128) / hn).astype(np.complex64)
+        y = np.zeros(j_end, dtype=np.complex128)
+        for i in range(j_end - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1: j_end] @ y[i + 1:]) / H[i, i]
+        d = d + V[:j_end].astype(np.complex128).T @ y
+        r = (s.astype(np.complex64) - matvec32(d.astype(np.complex64)))
+        est = np.linalg.norm(r.astype(np.complex128)) / ns
+        if est <= target or bd or k >= maxit_left:
+            return d, k, est, bd, hist
+
+
+def gmres_ir(matvec, matvec32, b, m=40, tol=1e-10, inner_reduction=1e-4, inner_maxit=5000, max_outer=20,
+             maxit=100000):
+    """FP64 iterative refinement around ``gmres_inner_c64`` (GMRES-IR with a complex64 inner
+    solve, after Carson & Higham 2018): r = b - A x in FP64, inner GMRES(m) on A d = r / ||r||
+    to an inner reduction `inner_reduction` (or the outer target, whichever is larger), x +=
+    ||r|| d in FP64; stop at true rel-res <= tol, after max_outer refinement steps or maxit inner
+    steps. Returns (x, Stats, outer, per-step list of (inner steps, true rel-res))."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b)
+    st = Stats()
+    nb = nrm2(b)
+    log, outer = [], 0
+    if nb == 0:
+        st.converged, st.relres = True, 0.0
+        return x, st, outer, log
+    while True:
+        r = b - matvec(x)
+        rel = nrm2(r) / nb
+        st.relres = rel
+        if rel <= tol:
+            st.converged = True
+            return x, st, outer, log
+        if outer >= max_outer or st.iterations >= maxit:
+            return x, st, outer, log
+        outer += 1
+        rn = rel * nb
+        target = max(inner_reduction, 0.5 * tol * nb / rn)
+        d, k, est, bd, hist = gmres_inner_c64(matvec32, r / rn, m, target, min(inner_maxit, maxit - st.iterations))
+        st.iterations += k
+        st.history += [h * rel for h in hist]
+        x = x + rn * d
+        log.append((k, float(nrm2(b - matvec(x)) / nb)))

@@ -29,7 +29,8 @@ HELM_PRECOND_NONE, HELM_PRECOND_RAS, HELM_PRECOND_JACOBI, HELM_PRECOND_ORAS = 0,
 EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary", "helm_sizes",
             "helm_assemble", "helm_matrix_free", "helm_matrix_csr", "helm_matrix_dia27", "helm_spmv", "helm_reduce",
             "helm_solve", "helm_solve_batch", "helm_adjoint_grad", "helm_adjoint_seed", "helm_last_profile",
-            "helm_reduce_noalloc", "helm_assemble_shared", "helm_shared_free", "helm_spmv_multi"]
+            "helm_reduce_noalloc", "helm_assemble_shared", "helm_shared_free", "helm_spmv_multi",
+            "helm_probe_fp64_fma"]
 
 
 class HelmError(RuntimeError):
@@ -100,6 +101,7 @@ def _load():
         "helm_assemble_shared": (i32, [vp, i32, P(vp)]),
         "helm_shared_free": (None, [vp]),
         "helm_spmv_multi": (i32, [vp, P(d), i32, vp, vp, vp]),
+        "helm_probe_fp64_fma": (i32, [i32, P(d), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -398,6 +400,13 @@ def helm_last_profile() -> dict:
     pr = Profile()
     _check(LIB.helm_last_profile(ctypes.byref(pr)))
     return pr.as_dict()
+
+
+def helm_probe_fp64_fma(iters: int = 20000, stream=None) -> float:
+    """Measured FP64 fused multiply-add rate of the device (FMA/s)."""
+    out = ctypes.c_double()
+    _check(LIB.helm_probe_fp64_fma(int(iters), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 class HelmSolve(torch.autograd.Function):

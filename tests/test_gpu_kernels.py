@@ -183,3 +183,12 @@ def test_sampled_rows_at_cabin_size():
     D = (S[rows] - Aref[rows])
     assert abs(D).max() <= 1e-14 * abs(Aref).max()
     assert np.max(np.abs(b - bref)) <= 1e-14 * np.max(np.abs(bref))
+
+
+def test_fp64_fma_probe():
+    # the library's FP64 FMA probe gives a finite, plausible rate (GB300: about 0.6e12 FMA/s)
+    # and rejects bad arguments
+    rate = helm.helm_probe_fp64_fma(2000)
+    assert 1e10 < rate < 1e14
+    out = helm.ctypes.c_double()
+    assert helm.LIB.helm_probe_fp64_fma(0, helm.ctypes.byref(out), None) == helm.HELM_ERR_ARG

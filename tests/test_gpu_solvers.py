@@ -144,8 +144,10 @@ def test_gmres_stagnation_matches_oracle():
 
 
 @pytest.mark.parametrize("dims,parts,f", [((12, 10, 8), (3, 2, 2), 200.0), ((25, 14, 12), (4, 2, 2), 100.0),
-                                          ((6, 5, 4), (1, 1, 1), 150.0)])
+                                          ((6, 5, 4), (1, 1, 1), 150.0), ((34, 19, 16), (8, 4, 4), 100.0)])
 def test_gmres_ras_matches_oracle(dims, parts, f):
+    # the last case: the 8 x 4 x 4 decomposition of the 282k cabin workload on a coarser cabin
+    # (128 subdomains, one CTA each)
     prob = hi.cabin_problem(*dims) if dims[0] > 20 else hi.small_box_problem(*dims)
     ctx = context(prob)
     o = helm.make_opts("gmres", restart=50, tol=1e-10, maxit=5000, precond="ras", ras_parts=parts, ras_overlap=2)

@@ -43,3 +43,15 @@ def test_adjoint_gradient_matches_central_differences():
             fd = (Jp - Jm) / (2 * h)
             an = gd[t].real if unit == 1.0 else gd[t].imag
             assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-3 * np.abs(gd).max())
+
+
+def test_dense_and_sparse_adjoints_agree():
+    # the dense LU form (the plain definition of the solves) and the sparse LU form give the same
+    # objective and gradients to rounding
+    prob = hi.small_box_problem(8, 6, 5)
+    w = hi.listener_weights(prob.mesh, centre=(0.5, 0.4, 0.3), radius=0.2)
+    J1, gb1, gd1, _ = adjoint.objective_and_gradient(prob, [100.0, 170.0], w)
+    J2, gb2, gd2, _ = adjoint.objective_and_gradient(prob, [100.0, 170.0], w, dense=True)
+    assert abs(J1 - J2) <= 1e-12 * J1
+    assert np.linalg.norm(gb1 - gb2) <= 1e-11 * np.linalg.norm(gb1)
+    assert np.linalg.norm(gd1 - gd2) <= 1e-11 * np.linalg.norm(gd1)

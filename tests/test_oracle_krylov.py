@@ -305,3 +305,30 @@ def test_refined_cocg_falls_back_to_cocg_when_refinement_stalls():
     assert outer == -4 and st.converged
     assert st.iterations == 32 + stc.iterations
     assert np.array_equal(x, xc)
+
+
+@pytest.mark.parametrize("dims,f", [((6, 4, 3), 230.0), ((10, 8, 6), 100.0)])
+def test_gmres_ir_complex64_inner_matches_dense_lu(dims, f):
+    # FP64 refinement around a complex64 inner GMRES(40) reaches the FP64 solution: each
+    # refinement step multiplies the FP64 residual by about the inner reduction
+    prob = hi.small_box_problem(*dims)
+    A, b = fem.system(prob, f)
+    ref = np.linalg.solve(A.toarray(), b)
+    A32 = A.astype(np.complex64)
+    x, st, outer, log = krylov.gmres_ir(lambda v: A @ v, lambda v: A32 @ v, b, m=40, tol=1e-12)
+    assert st.converged and outer >= 2
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+    rels = [r for _, r in log]
+    assert all(r2 < r1 for r1, r2 in zip(rels, rels[1:]))
+    assert rels[0] <= 1e-3  # the first inner solve alone reaches the inner reduction (1e-4) to the
+    #                         accuracy complex64 allows
+
+
+def test_gmres_inner_complex64_stops_at_its_target():
+    prob = hi.small_box_problem(6, 4, 3)
+    A, b = fem.system(prob, 150.0)
+    A32 = A.astype(np.complex64)
+    s = b / np.linalg.norm(b)
+    d, k, est, bd, hist = krylov.gmres_inner_c64(lambda v: A32 @ v, s, 40, 1e-4, 10000)
+    assert est <= 1e-4 and not bd
+    assert np.linalg.norm(s - A @ d) <= 2e-4  # the FP64 residual of the correction, to complex64 accuracy
