@@ -570,6 +570,9 @@ def run_gpu(args):
                           "relres_max": max(s["relres"] for s in stats)},
            "phases_ms": {"assemble": prof["assemble_ms"], "solve": prof["solve_ms"]},
            "roofline": roof,
+           "launch": {"grid_blocks": prof["grid_blocks"], "tiles": prof["ntiles"],
+                      "knobs": {k: int(os.environ.get(k, v)) for k, v in autotune_defaults().items()},
+                      "chosen_by": "bench.py --autotune on this workload (profiles/autotune_sweep256.md)"},
            "fp64_peak": {"fma_per_s": fp64_fma, "tflops": fp64_tflops,
                          "how": "helm_probe_fp64_fma: 8 independent FMA chains per thread, 16 blocks of 256 per SM, "
                                 "CUDA events"},
@@ -810,6 +813,11 @@ def run_configs(args):
         peaks, _ = measured_peaks()
         res["spmm_cabin2m"] = spmm_multi_roofline(helm, torch, float(peaks["hbm_gbs"]))
     print(json.dumps({"configs": res}), flush=True)
+
+
+def autotune_defaults():
+    from paper_2112_00087_gb300 import autotune
+    return dict(autotune.DEFAULTS)
 
 
 def run_autotune(args):
