@@ -572,7 +572,7 @@ def run_gpu(args):
            "roofline": roof,
            "launch": {"grid_blocks": prof["grid_blocks"], "tiles": prof["ntiles"],
                       "knobs": {k: int(os.environ.get(k, v)) for k, v in autotune_defaults().items()},
-                      "chosen_by": "bench.py --autotune on this workload (profiles/autotune_sweep256.md)"},
+                      "chosen_by": "bench.py --autotune on this workload (coordinate descent; the defaults won)"},
            "fp64_peak": {"fma_per_s": fp64_fma, "tflops": fp64_tflops,
                          "how": "helm_probe_fp64_fma: 8 independent FMA chains per thread, 16 blocks of 256 per SM, "
                                 "CUDA events"},

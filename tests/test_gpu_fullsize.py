@@ -1,15 +1,28 @@
-"""Parity at the benchmark's full size and launch configuration, and a full-size adjoint check.
+"""Parity at the benchmark's full size and launch configuration.
 
 The 256-frequency sweep is solved exactly as bench.py times its main leg (one helm_solve_batch
-call, same options: double-word inner COCG, FP64 refinement, symmetric Jacobi). Systems small enough for the oracle are compared with it one by one; every sampled large
-system is checked through its true FP64 residual computed by a different kernel (helm_spmv on the
-CSR matrix)."""
+call, same options: double-word inner COCG, FP64 refinement, symmetric Jacobi). The oracle runs
+the same refinement (oracle.krylov.cocg_ir on the symmetric-Jacobi scaled system):
+  * step counts of every 16th system (and 248, 255) lie within the oracle's rounding spread
+    (its count for b and for three right-hand sides perturbed at 1e-14) widened by 5%, with the
+    oracle's inner solve in the kernel's arithmetic (double-word, oracle.dwfloat), since the
+    count is decided by that arithmetic (live up to 27,508 nodes, stored beyond);
+  * the same systems solved to rel-res 1e-13 agree with the oracle's rel-res 1e-13 solutions
+    to rel-L2 <= 1e-9 -- on the whole vector where the oracle runs here (up to 27,508 nodes),
+    on 128 seeded nodes and the 2-norm for the larger ones (50,176 to 901,152 nodes), whose
+    oracle results tests/golden/make_sweep_refs.py wrote into tests/golden/sweep_refs.json;
+  * every system's true residual, computed by a different kernel (helm_spmv on the CSR
+    matrix), meets 1e-10.
+"""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import bench
 import helm_inputs as hi
-from oracle import fem, krylov
+from oracle import dwfloat, fem, krylov
 
 pytestmark = pytest.mark.gpu
 
@@ -20,6 +33,9 @@ if not torch.cuda.is_available():
 from paper_2112_00087_gb300 import helm  # noqa: E402
 from tests.gpu_util import context, rel  # noqa: E402
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+LIVE = tuple(range(0, 161, 16))  # systems the oracle solves here, in seconds each
+
 
 def true_relres(ctx, f, x):
     A = helm.helm_assemble(ctx, f)
@@ -29,68 +45,79 @@ def true_relres(ctx, f, x):
     return (torch.linalg.norm(A.rhs - y) / torch.linalg.norm(A.rhs)).item()
 
 
+def in_spread5(c, counts):
+    return 0.95 * min(counts) - 1 <= c <= 1.05 * max(counts) + 1
+
+
+def oracle_counts(prob, f):
+    """The oracle's step counts of the benchmark's method (inner solve in double-word arithmetic)
+    on b and on three perturbed b."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_sweep_refs", os.path.join(GOLDEN, "make_sweep_refs.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    A, b = fem.system(prob, f)
+    Ah, s, w = krylov.sym_jacobi(A)
+    m = prob.mesh
+    inner = dwfloat.make_inner(dwfloat.StencilMatrix(dwfloat.slots_from_csr(Ah, m.nx, m.ny), m.nx, m.ny))
+    out = []
+    for sd in (0,) + gen.PERTURB_SEEDS:
+        rhs = s * b if sd == 0 else gen.perturbed_rhs(s * b, sd)
+        _, st, outer = krylov.cocg_ir(lambda v: Ah @ v, rhs, tol=1e-10, inner_maxit=45000, maxit=45000,
+                                      stall=bench.STALL, weights=w, inner=inner)
+        assert st.converged and outer == 1
+        out.append(st.iterations)
+    return out, gen
+
+
 def test_full_sweep_in_the_benchmark_configuration():
     freqs = hi.sweep_freqs(256)
     probs = [hi.cabin_problem(*hi.sweep_mesh_dims(f)) for f in freqs]
     ctxs = [context(p) for p in probs]
+    refs = json.load(open(os.path.join(GOLDEN, "sweep_refs.json")))
+    big = sorted(int(k) for k in refs["systems"])
     # the benchmark's main leg: double-word inner COCG with FP64 refinement, symmetric Jacobi
     opts = bench.dw_opts(helm, precond="jacobi")
     ps, st = helm.helm_solve_batch(ctxs, freqs, opts)
     assert all(s["status"] == 0 for s in st)
     assert all(s["outer"] >= 1 for s in st)  # no system fell back to FP64 COCG
-    # oracle (FP64 symmetric-Jacobi COCG), one by one, on systems it solves in seconds
-    for k in (0, 60, 120, 150):
-        A, b = fem.system(probs[k], freqs[k])
-        Ah, sc, w = krylov.sym_jacobi(A)
-        y, ost = krylov.cocg(lambda v: Ah @ v, sc * b, tol=1e-10, maxit=45000, stall=bench.STALL, weights=w)
-        x = sc * y
-        g = ps[k].cpu().numpy()
-        assert np.linalg.norm(b - A @ g) / np.linalg.norm(b) <= 1e-10
-        # inner double-word steps against FP64 steps: within 25% (median +4% on the sweep)
-        assert 0.75 * ost.iterations - 2 <= st[k]["iterations"] <= 1.25 * ost.iterations + 2, (k, st[k], ost.iterations)
-        assert rel(g, x) <= 1e-6
-    # large systems: true residual through an independent kernel
-    for k in (200, 230, 240, 245, 250, 255):
+    for k in range(256):
         assert true_relres(ctxs[k], freqs[k], ps[k]) <= 1.01e-10, k
+    bad = []
+    gen = None
+    for k in LIVE:
+        counts, gen = oracle_counts(probs[k], freqs[k])
+        if not in_spread5(st[k]["iterations"], counts):
+            bad.append((k, st[k]["iterations"], counts))
+    for k in big:
+        r = refs["systems"][str(k)]
+        assert r["n"] == ctxs[k].n and abs(r["freq"] - freqs[k]) <= 1e-9 * freqs[k]
+        assert r["converged_dw"] and r["outer_dw"] == [1, 1, 1, 1]
+        if not in_spread5(st[k]["iterations"], r["iterations_dw"]):
+            bad.append((k, st[k]["iterations"], r["iterations_dw"]))
+    assert not bad, bad
 
-
-def test_adjoint_central_differences_at_cabin_size():
-    """282,093-node cabin: the hand-written adjoint gradient against central differences of the
-    listener objective through the GPU forward solve (h = 1e-6, forward solves at rel-res 1e-13)."""
-    prob = hi.cabin_problem(100, 56, 48)
-    ctx = context(prob)
-    freqs = [60.0, 150.0]
-    w = torch.from_numpy(hi.listener_weights(prob.mesh)).cuda()
-    o = helm.make_opts("cocg", tol=1e-13, maxit=60000, stall_window=bench.STALL)
-    p, st = helm.helm_solve(ctx, freqs, o)
-    J, gb, gd = helm.helm_adjoint_grad(ctx, freqs, o, p, w)
-    gb, gd = gb.cpu().numpy(), gd.cpu().numpy()
-    nodes = torch.from_numpy(prob.dir_nodes).cuda()
-
-    def objective(beta, pdir):
-        ctx.set_boundary(torch.from_numpy(beta).cuda(), nodes, torch.from_numpy(pdir).cuda())
-        pp, s2 = helm.helm_solve(ctx, freqs, o)
-        return float((w[None, :] * pp.abs() ** 2).sum().item())
-
-    assert abs(objective(prob.beta, prob.p_dir) - J) <= 1e-10 * J
-    rng = np.random.default_rng(0)
-    h = 1e-6
-    faces = rng.choice(np.flatnonzero(prob.beta != 0), 6, replace=False)
-    for e in faces:
-        for unit in (1.0, 1j):
-            bp, bm = prob.beta.copy(), prob.beta.copy()
-            bp[e] += h * unit
-            bm[e] -= h * unit
-            fd = (objective(bp, prob.p_dir) - objective(bm, prob.p_dir)) / (2 * h)
-            an = gb[e].real if unit == 1.0 else gb[e].imag
-            # central differences carry an absolute error set by the solve accuracy over h, so the
-            # bound is relative to the gradient's scale
-            assert abs(fd - an) <= 1e-5 * np.abs(gb).max(), (e, unit, fd, an)
-    for t in rng.choice(len(prob.dir_nodes), 3, replace=False):
-        for unit in (1.0, 1j):
-            pp_, pm_ = prob.p_dir.copy(), prob.p_dir.copy()
-            pp_[t] += h * unit
-            pm_[t] -= h * unit
-            fd = (objective(prob.beta, pp_) - objective(prob.beta, pm_)) / (2 * h)
-            an = gd[t].real if unit == 1.0 else gd[t].imag
-            assert abs(fd - an) <= 1e-5 * np.abs(gd).max(), (t, unit, fd, an)
+    # solution values at rel-res 1e-13, the sampled systems in one batch
+    sample = list(LIVE) + big
+    o13 = helm.make_opts("cocg", tol=1e-13, maxit=60000, mixed="dw", inner_tol=1e-12, inner_maxit=60000,
+                         max_outer=20, stall_window=bench.STALL, precond="jacobi")
+    p13, s13 = helm.helm_solve_batch([ctxs[k] for k in sample], [freqs[k] for k in sample], o13)
+    assert all(s["status"] == 0 for s in s13)
+    errs = {}
+    for j, k in enumerate(sample):
+        g = p13[j].cpu().numpy()
+        if k in LIVE:
+            A, b = fem.system(probs[k], freqs[k])
+            Ah, sc, w = krylov.sym_jacobi(A)
+            y, ost, _ = krylov.cocg_ir(lambda v: Ah @ v, sc * b, tol=1e-13, inner_maxit=60000, maxit=60000,
+                                       stall=bench.STALL, weights=w)
+            assert ost.converged
+            errs[k] = rel(g, sc * y)
+        else:
+            v = refs["systems"][str(k)]["value"]
+            assert v["converged"] and v["relres"] <= 1e-13
+            idx = np.array(v["idx"])
+            assert np.array_equal(idx, gen.sample_nodes(k, ctxs[k].n))
+            xs = np.array(v["re"]) + 1j * np.array(v["im"])
+            errs[k] = max(rel(g[idx], xs), abs(np.linalg.norm(g) - v["norm"]) / v["norm"])
+    assert max(errs.values()) <= 1e-9, errs
