@@ -820,6 +820,50 @@ def autotune_defaults():
     return dict(autotune.DEFAULTS)
 
 
+def run_autotune_kernels(args):
+    """Coordinate search of the standalone kernels' knobs (CSR lanes per row, reduction partials)
+    on the 2,203,161-node lattice: the objective is the sum of the median times (L2 flushed) of a
+    complex128 CSR product, a complex64 CSR product and an unconjugated dot product."""
+    import torch
+    from paper_2112_00087_gb300 import autotune, helm
+    pr = hi.cabin_problem(200, 112, 96)
+    m = pr.mesh
+    ctx = helm.Context(m.nx, m.ny, m.nz, m.Lx, m.Ly, m.Lz)
+    ctx.set_boundary(torch.from_numpy(pr.beta).cuda(), torch.from_numpy(pr.dir_nodes).cuda(),
+                     torch.from_numpy(pr.p_dir).cuda())
+    A128 = helm.helm_assemble(ctx, 250.0, helm.HELM_C128, with_rhs=False)
+    A64 = helm.helm_assemble(ctx, 250.0, helm.HELM_C64, with_rhs=False)
+    x128 = torch.randn(ctx.n, dtype=torch.complex128, device="cuda")
+    x64 = x128.to(torch.complex64)
+    y128, y64 = torch.empty_like(x128), torch.empty_like(x64)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def med(fn, reps=7):
+        times = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(times)
+
+    def run():
+        t = med(lambda: helm.helm_spmv(A128, x128, y128)) + med(lambda: helm.helm_spmv(A64, x64, y64))
+        t0 = time.perf_counter()
+        for _ in range(5):
+            helm.helm_reduce(1, x128, x128)
+        return t + (time.perf_counter() - t0) / 5
+
+    run()
+    best, log = autotune.autotune(run, space=autotune.KERNEL_SPACE, start=autotune.KERNEL_DEFAULTS)
+    print(json.dumps({"autotune_kernels": {"best": best, "trials": [{"config": c, "time_s": t} for c, t in log]}}),
+          flush=True)
+
+
 def run_autotune(args):
     """Coordinate search of the launch-shape knobs for the main leg on the chosen workload."""
     import torch
@@ -886,6 +930,8 @@ def main():
                          "ras282k cabin2m cabin2m32 adjoint64 resonance64 spmm)")
     ap.add_argument("--autotune", action="store_true",
                     help="search the persistent engine's launch-shape knobs on this workload (one line of JSON)")
+    ap.add_argument("--autotune-kernels", action="store_true",
+                    help="search the standalone SpMV / reduction knobs on the 2.2 M-node lattice (one line of JSON)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes (read + write) of one persistent launch from an ncu capture, if known")
     args = ap.parse_args()
@@ -893,6 +939,8 @@ def main():
         run_reference(args)
     elif args.autotune:
         run_autotune(args)
+    elif args.autotune_kernels:
+        run_autotune_kernels(args)
     elif args.configs is not None:
         run_configs(args)
     else:

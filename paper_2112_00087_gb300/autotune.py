@@ -31,6 +31,16 @@ SPACE: Dict[str, Sequence[int]] = {
 }
 
 
+# Knobs of the standalone kernels (read at every call): lanes per row of the CSR product for
+# complex128 and complex64, and the partial sums per SM of helm_reduce.
+KERNEL_DEFAULTS: Dict[str, int] = {"HELM_SPMV_LANES_C128": 4, "HELM_SPMV_LANES_C64": 8, "HELM_REDUCE_PARTS_PER_SM": 1}
+KERNEL_SPACE: Dict[str, Sequence[int]] = {
+    "HELM_SPMV_LANES_C128": (2, 4, 8, 16),
+    "HELM_SPMV_LANES_C64": (2, 4, 8, 16),
+    "HELM_REDUCE_PARTS_PER_SM": (1, 2, 4, 8, 16),
+}
+
+
 def apply(config: Dict[str, int]) -> None:
     """Install a setting for the solves that follow in this process."""
     for k, v in config.items():

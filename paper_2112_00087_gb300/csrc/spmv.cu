@@ -2,6 +2,7 @@
 // deterministic FP64 reductions (dot products / norms of the Krylov methods).
 #include <algorithm>
 #include <mutex>
+#include <cstdlib>
 #include <string>
 
 #include "kernels.cuh"
@@ -109,24 +110,37 @@ __global__ void __launch_bounds__(kBlock) reduce_stage2(const double* __restrict
 
 }  // namespace
 
-helm_status spmv_c128(const int32_t* rowptr, const int32_t* col, const cd* val, const cd* x, cd* y,
-                      int64_t n, cudaStream_t s) {
+// Lanes per row of the CSR product (tuning knobs HELM_SPMV_LANES_C128 / _C64: 2, 4, 8 or 16;
+// defaults 4 and 8, the autotuner's choice on the 2.2 M-node lattice).
+static int spmv_lanes(const char* env, int def) {
+  const char* e = getenv(env);
+  const int g = e ? atoi(e) : def;
+  return (g == 2 || g == 4 || g == 8 || g == 16) ? g : def;
+}
+
+template <typename T>
+static helm_status spmv_csr(int G, const int32_t* rowptr, const int32_t* col, const cplx<T>* val, const cplx<T>* x,
+                            cplx<T>* y, int64_t n, cudaStream_t s) {
   if (n == 0) return HELM_OK;
-  constexpr int G = 4;
-  int64_t blocks = std::min<int64_t>((n + kBlock / G - 1) / (kBlock / G), (int64_t)num_sms() * 8);
-  spmv_kernel<G, double><<<(unsigned)blocks, kBlock, 0, s>>>(rowptr, col, val, x, y, n);
+  const int64_t blocks = std::min<int64_t>((n + kBlock / G - 1) / (kBlock / G), (int64_t)num_sms() * 8);
+  switch (G) {
+    case 2: spmv_kernel<2, T><<<(unsigned)blocks, kBlock, 0, s>>>(rowptr, col, val, x, y, n); break;
+    case 4: spmv_kernel<4, T><<<(unsigned)blocks, kBlock, 0, s>>>(rowptr, col, val, x, y, n); break;
+    case 8: spmv_kernel<8, T><<<(unsigned)blocks, kBlock, 0, s>>>(rowptr, col, val, x, y, n); break;
+    default: spmv_kernel<16, T><<<(unsigned)blocks, kBlock, 0, s>>>(rowptr, col, val, x, y, n); break;
+  }
   HELM_CUDA(cudaGetLastError());
   return HELM_OK;
 }
 
+helm_status spmv_c128(const int32_t* rowptr, const int32_t* col, const cd* val, const cd* x, cd* y,
+                      int64_t n, cudaStream_t s) {
+  return spmv_csr<double>(spmv_lanes("HELM_SPMV_LANES_C128", 4), rowptr, col, val, x, y, n, s);
+}
+
 helm_status spmv_c64(const int32_t* rowptr, const int32_t* col, const cf* val, const cf* x, cf* y,
                      int64_t n, cudaStream_t s) {
-  if (n == 0) return HELM_OK;
-  constexpr int G = 8;
-  int64_t blocks = std::min<int64_t>((n + kBlock / G - 1) / (kBlock / G), (int64_t)num_sms() * 8);
-  spmv_kernel<G, float><<<(unsigned)blocks, kBlock, 0, s>>>(rowptr, col, val, x, y, n);
-  HELM_CUDA(cudaGetLastError());
-  return HELM_OK;
+  return spmv_csr<float>(spmv_lanes("HELM_SPMV_LANES_C64", 8), rowptr, col, val, x, y, n, s);
 }
 
 helm_status spmv_dia_c128(const cd* val, const uint8_t* cflag, const cd* x, cd* y, int64_t n, int64_t Nx,
@@ -148,7 +162,11 @@ helm_status spmv_dia_c64(const cf* val, const uint8_t* cflag, const cf* x, cf* y
 }
 
 helm_status reduce_c128(int op, int64_t n, const cd* x, const cd* y, double* out_host, cudaStream_t s) {
-  const int nparts = std::max(1, std::min<int>(num_sms() * 4, (int)((n + kBlock - 1) / kBlock)));
+  // partial sums per SM (tuning knob HELM_REDUCE_PARTS_PER_SM, 1..64; default 1, the autotuner's
+  // choice on the 2.2 M-node lattice)
+  const char* penv = getenv("HELM_REDUCE_PARTS_PER_SM");
+  const int per_sm = penv ? std::max(1, std::min(atoi(penv), 64)) : 1;
+  const int nparts = std::max(1, std::min<int>(num_sms() * per_sm, (int)((n + kBlock - 1) / kBlock)));
   const int64_t chunk = (n + nparts - 1) / nparts;
   double* buf = nullptr;
   helm_status st = dev_alloc(&buf, 2 * (size_t)nparts + 2);
