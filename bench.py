@@ -389,11 +389,19 @@ def spmm_multi_roofline(helm, torch, peak_gbs, nfreqs=(8, 32)):
             passes = (F + 7) // 8
             b_multi = passes * (27 * n * vb + n) + F * 2 * vb * n
             b_single = F * dia_spmv_bytes(n, vb)
-            out["%s_F%d" % (name, F)] = {
-                "multi_ms_per_freq": t_multi / F * 1e3, "single_ms_per_freq": t_single / F * 1e3,
-                "speedup": t_single / t_multi, "multi_gbs": b_multi / t_multi / 1e9,
-                "multi_frac": b_multi / t_multi / 1e9 / peak_gbs, "single_gbs": b_single / t_single / 1e9,
-                "bytes_per_freq_multi": b_multi / F, "bytes_per_freq_single": b_single / F}
+            rec = {"multi_ms_per_freq": t_multi / F * 1e3, "single_ms_per_freq": t_single / F * 1e3,
+                   "speedup": t_single / t_multi, "multi_gbs": b_multi / t_multi / 1e9,
+                   "multi_frac": b_multi / t_multi / 1e9 / peak_gbs, "single_gbs": b_single / t_single / 1e9,
+                   "bytes_per_freq_multi": b_multi / F, "bytes_per_freq_single": b_single / F}
+            if F == 8:
+                # the frequency-interleaved layout ([n][8]): one 16-byte-vector block per neighbour
+                Xi = X.t().contiguous()
+                Yi = torch.empty_like(Xi)
+                t_il = timed_med(lambda: helm.helm_spmv_multi_interleaved(S, freqs, Xi, Yi))
+                rec.update({"interleaved_ms_per_freq": t_il / F * 1e3, "interleaved_speedup_vs_single": t_single / t_il,
+                            "interleaved_gbs": b_multi / t_il / 1e9, "interleaved_frac": b_multi / t_il / 1e9 / peak_gbs})
+                del Xi, Yi
+            out["%s_F%d" % (name, F)] = rec
             del X, Y
         S.close()
     ctx.close()

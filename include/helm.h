@@ -213,6 +213,15 @@ void helm_shared_free(helm_shared* S);
 helm_status helm_spmv_multi(const helm_shared* S, const double* freqs_hz, int32_t nfreq, const void* X,
                             void* Y, void* stream);
 
+/* The same products with X and Y node-major ("frequency-interleaved"): X[i * nfreq + f] is node
+ * i's value for frequency f, so one 16-byte-aligned block per node carries all frequencies and the
+ * product gathers each neighbour's block once (paper Sec. 3.1: the FRF evaluates the Sec. 3.2
+ * operator at many frequencies on one mesh). nfreq: 2, 4 or 8 for HELM_C64, 1, 2, 4 or 8 for
+ * HELM_C128 (HELM_ERR_ARG otherwise); X, Y (dev) 16-byte aligned, not overlapping; freqs_hz (host)
+ * >= 0. Ordered on `stream` (NULL = the context stream); does not synchronise. */
+helm_status helm_spmv_multi_interleaved(const helm_shared* S, const double* freqs_hz, int32_t nfreq,
+                                        const void* X, void* Y, void* stream);
+
 /* Reductions over complex128 vectors x, y (dev, [n]), FP64 accumulation in a fixed order:
  * op 0: x^H y (conjugated, GMRES), op 1: x^T y (unconjugated, COCG), op 2: ||x||_2 (y unused).
  * The result (host, double[2]) is written after the call synchronises `stream`. */

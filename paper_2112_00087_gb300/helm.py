@@ -30,7 +30,7 @@ EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary
             "helm_assemble", "helm_matrix_free", "helm_matrix_csr", "helm_matrix_dia27", "helm_spmv", "helm_reduce",
             "helm_solve", "helm_solve_batch", "helm_adjoint_grad", "helm_adjoint_seed", "helm_last_profile",
             "helm_reduce_noalloc", "helm_assemble_shared", "helm_shared_free", "helm_spmv_multi",
-            "helm_probe_fp64_fma"]
+            "helm_probe_fp64_fma", "helm_spmv_multi_interleaved"]
 
 
 class HelmError(RuntimeError):
@@ -102,6 +102,7 @@ def _load():
         "helm_shared_free": (None, [vp]),
         "helm_spmv_multi": (i32, [vp, P(d), i32, vp, vp, vp]),
         "helm_probe_fp64_fma": (i32, [i32, P(d), vp]),
+        "helm_spmv_multi_interleaved": (i32, [vp, P(d), i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -324,6 +325,18 @@ def helm_spmv_multi(S: SharedOperator, freqs: Sequence[float], X: torch.Tensor, 
     assert X.numel() == nf * S.n and Y.numel() == nf * S.n
     fr = (ctypes.c_double * max(1, nf))(*[float(f) for f in freqs])
     _check(LIB.helm_spmv_multi(S.handle, fr, nf, _ptr(X), _ptr(Y), _stream(stream)))
+
+
+def helm_spmv_multi_interleaved(S: SharedOperator, freqs: Sequence[float], X: torch.Tensor, Y: torch.Tensor,
+                                stream=None):
+    """Y[i, f] = (A(freqs[f]) X[:, f])_i; X, Y [n, nfreq] contiguous (node-major), complex in the
+    precision of S; nfreq 2, 4, 8 (complex64) or 1, 2, 4, 8 (complex128)."""
+    want = torch.complex64 if S.precision == HELM_C64 else torch.complex128
+    nf = len(freqs)
+    assert X.dtype == want and Y.dtype == want and X.is_contiguous() and Y.is_contiguous()
+    assert X.numel() == nf * S.n and Y.numel() == nf * S.n
+    fr = (ctypes.c_double * max(1, nf))(*[float(f) for f in freqs])
+    _check(LIB.helm_spmv_multi_interleaved(S.handle, fr, nf, _ptr(X), _ptr(Y), _stream(stream)))
 
 
 def helm_reduce(op: int, x: torch.Tensor, y: Optional[torch.Tensor] = None, stream=None) -> complex:

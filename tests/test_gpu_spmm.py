@@ -95,3 +95,45 @@ def test_multi_frequency_argument_errors():
     # an empty batch is a no-op
     helm._check(helm.LIB.helm_spmv_multi(S.handle, (helm.ctypes.c_double * 1)(1.0), 0, None, None, None))
     S.close()
+
+
+@pytest.mark.parametrize("name,prob", CASES, ids=[c[0] for c in CASES])
+def test_interleaved_product_matches_oracle(name, prob):
+    # node-major X, Y ([n][F]): the same products as the frequency-major form, against the oracle
+    ctx = context(prob)
+    n = ctx.n
+    for prec, tol, nfs in ((helm.HELM_C128, 1e-13, (1, 2, 4, 8)), (helm.HELM_C64, 64 * 2.0 ** -24, (2, 4, 8))):
+        S = helm.helm_assemble_shared(ctx, prec)
+        dt = torch.complex128 if prec == helm.HELM_C128 else torch.complex64
+        for F in nfs:
+            freqs = FREQS[:F]
+            X = np.stack([hi.random_complex(n, seed=31 + f) for f in range(F)], axis=1)  # [n][F]
+            Xg = torch.from_numpy(X).to(dt).cuda().contiguous()
+            Yg = torch.empty_like(Xg)
+            helm.helm_spmv_multi_interleaved(S, freqs, Xg, Yg)
+            torch.cuda.synchronize()
+            Y = Yg.cpu().numpy().astype(np.complex128)
+            KM = fem.assemble_KM(prob.mesh)
+            for f, fr in enumerate(freqs):
+                A, _ = fem.system(prob, fr, KM)
+                ref = A @ X[:, f]
+                bound = abs(A) @ np.abs(X[:, f])
+                err = np.abs(Y[:, f] - ref)
+                assert np.all(err <= tol * bound + 1e-30), (prec, F, fr)
+        S.close()
+
+
+def test_interleaved_product_arguments():
+    ctx = context(hi.small_box_problem(6, 4, 3))
+    S = helm.helm_assemble_shared(ctx, helm.HELM_C64)
+    X = torch.zeros(ctx.n, 3, dtype=torch.complex64, device="cuda")
+    Y = torch.zeros_like(X)
+    with pytest.raises(helm.HelmError):  # 3 frequencies: not a supported block width
+        helm._check(helm.LIB.helm_spmv_multi_interleaved(S.handle, (helm.ctypes.c_double * 3)(1.0, 2.0, 3.0), 3,
+                                                          helm._ptr(X), helm._ptr(Y), None))
+    X4 = torch.zeros(ctx.n * 4 + 2, dtype=torch.complex64, device="cuda")
+    with pytest.raises(helm.HelmError):  # misaligned (8-byte offset)
+        helm._check(helm.LIB.helm_spmv_multi_interleaved(S.handle, (helm.ctypes.c_double * 4)(1.0, 2.0, 3.0, 4.0), 4,
+                                                          helm._ptr(X4[1:]), helm._ptr(Y), None))
+    S.close()
+
