@@ -163,17 +163,21 @@ __device__ __forceinline__ int vload(const int* p) { return *((volatile const in
 // Dynamic tile scheduling of one phase: blocks take the entries of the active tile list in order
 // from the phase's counter, one atomic per tile, so a block that finishes early takes more tiles
 // and every block reaches the grid barrier at about the same time. While the list holds more
-// than two tiles per block the next entry is requested as the current tile starts (hiding the
-// atomic's latency); with fewer it is requested after the tile, so no block holds a tile that an
-// idle block could have taken. Results do not depend on which block processes a tile (partial
+// than two tiles per block (and may_look_ahead) the next entry is requested as the current tile
+// starts (hiding the atomic's latency); with fewer it is requested after the tile, so no block
+// holds a tile that an idle block could have taken. A phase whose tiles are long next to the
+// atomic's latency passes may_look_ahead = false: a request made as a tile starts can leave a
+// block holding one more tile at the end of the phase while others already wait at the barrier.
+// Results do not depend on which block processes a tile (partial
 // sums are combined in tile order). Counter g % CTRL_NQ of phase g (three phases per super-step)
 // is zeroed by block 0 in phase g + 3, between two barriers on either side of its uses; the host
 // starts them at zero.
 template <typename F>
-__device__ __forceinline__ void for_tiles_dynamic(const KParams& P, int phase_g, int nat, const int* list, F f) {
+__device__ __forceinline__ void for_tiles_dynamic(const KParams& P, int phase_g, int nat, const int* list, F f,
+                                                  bool may_look_ahead = true) {
   __shared__ int s_a;
   int* ctr = P.ctrl + CTRL_Q0 + phase_g % CTRL_NQ;
-  const bool ahead = nat > 2 * (int)gridDim.x;
+  const bool ahead = may_look_ahead && nat > 2 * (int)gridDim.x;
   if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl[CTRL_Q0 + (phase_g + 3) % CTRL_NQ] = 0;
   if (threadIdx.x == 0) s_a = atomicAdd(ctr, 1);
   __syncthreads();
