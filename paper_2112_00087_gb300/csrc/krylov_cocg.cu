@@ -603,9 +603,12 @@ __device__ __forceinline__ void tile_spmv_dw(const KSys& Y, const cw* x, int64_t
   int has_c = 0;
   const int64_t ahead = (int64_t)pf * kBlock;
   for (int64_t r0 = row0 + threadIdx.x; r0 < row1; r0 += kBlock) {
-    if (pf && r0 + ahead < row1)
+    if (pf && r0 + ahead < row1) {
 #pragma unroll
       for (int k = 0; k < 27; ++k) prefetch_l2(Y.valw + (int64_t)k * ns + r0 + ahead);
+      const int64_t up = r0 + ahead + NxNy;  // x of the plane above, first touched by this tile
+      if (up < n) prefetch_l2(x + up);
+    }
     const cw s0 = (r0 >= reach && r0 + reach < n) ? dia_row_re_dw2<false>(Y.valw, x, n, ns, Nx, NxNy, r0)
                                                   : dia_row_re_dw2<true>(Y.valw, x, n, ns, Nx, NxNy, r0);
     const int c0 = Y.cflag[r0];
