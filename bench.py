@@ -740,6 +740,22 @@ def run_configs(args):
                                  "dw_jacobi": {"freqs_per_s": len(fr) / dtdw, "iterations": [s_["iterations"] for s_ in stdw],
                                                "status": [s_["status"] for s_ in stdw], "rel_l2_vs_fp64": err_dw}}
         del p64, pmx, pdw
+    if want("schwarz282k"):
+        # Schwarz variants on the 282k cabin, GMRES(50), 8x4x4 blocks, overlap 0 and 2, 100 and
+        # 200 Hz: plain RAS, one-sided Robin interfaces (i k), two-sided (e^{+-3i pi/4} / h)
+        c = ctx_of(hi.cabin_problem(100, 56, 48))
+        two = (np.exp(0.75j * np.pi), np.exp(-0.75j * np.pi))
+        out = {}
+        for f in (100.0, 200.0):
+            for ov in (0, 2):
+                for name, pc, rb in (("ras", "ras", None), ("oras", "oras", None), ("oras2", "oras2", two)):
+                    o = helm.make_opts("gmres", restart=50, tol=TOL, maxit=5000, precond=pc, ras_parts=(8, 4, 4),
+                                       ras_overlap=ov, robin=rb)
+                    _, st, dt, pr_ = run(c, [f], o)
+                    out["%g Hz overlap %d %s" % (f, ov, name)] = {
+                        "ms_total": dt * 1e3, "solve_ms": pr_["solve_ms"], "iterations": st[0]["iterations"],
+                        "relres": st[0]["relres"], "status": st[0]["status"]}
+        res["schwarz282k"] = out
     if want("ras282k"):
         # one GMRES(50) + RAS 8x4x4 (overlap 2) solve of the 282k cabin at 100 Hz (profiling case)
         c = ctx_of(hi.cabin_problem(100, 56, 48))
@@ -935,7 +951,7 @@ def main():
     ap.add_argument("--verbose", action="store_true", help="per-system statistics on stderr")
     ap.add_argument("--configs", nargs="*", default=None,
                     help="measure the secondary workloads instead (all, or the named ones: box100 cabin282k "
-                         "ras282k cabin2m cabin2m32 adjoint64 resonance64 spmm)")
+                         "ras282k schwarz282k cabin2m cabin2m32 adjoint64 resonance64 spmm)")
     ap.add_argument("--autotune", action="store_true",
                     help="search the persistent engine's launch-shape knobs on this workload (one line of JSON)")
     ap.add_argument("--autotune-kernels", action="store_true",

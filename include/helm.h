@@ -65,7 +65,8 @@ typedef enum {
 enum { HELM_C128 = 0, HELM_C64 = 1 };                 /* matrix value precision */
 enum { HELM_FMT_CSR = 0, HELM_FMT_DIA27 = 1 };         /* matrix layout (see helm_assemble) */
 enum { HELM_SOLVER_GMRES = 0, HELM_SOLVER_COCG = 1, HELM_SOLVER_BICGSTAB = 2, HELM_SOLVER_TFQMR = 3 }; /* Krylov method */
-enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1, HELM_PRECOND_JACOBI = 2, HELM_PRECOND_ORAS = 3 };
+enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_RAS = 1, HELM_PRECOND_JACOBI = 2, HELM_PRECOND_ORAS = 3,
+       HELM_PRECOND_ORAS2 = 4 };
 /* preconditioner (right, except the symmetric Jacobi form of COCG) */
 
 typedef struct {
@@ -83,6 +84,12 @@ typedef struct {
                            term i k M_G (face mass of the subdomain's faces inside the lattice,
                            Dirichlet nodes excluded; paper Sec. 4 names absorbing Robin interface
                            conditions, i k is the matched impedance of the wall term);
+                           HELM_PRECOND_ORAS2 (GMRES only): the two-sided form of the paper's
+                           optimized Schwarz method (Sec. 4: different interface conditions on
+                           the two sides of an interface): each subdomain matrix carries
+                           (robin_lo / h_a) M_face on the low faces of its extended box (planes
+                           i0, j0, l0) and (robin_hi / h_a) M_face on its high faces, h_a the
+                           lattice spacing normal to the face, Dirichlet nodes excluded;
                            HELM_PRECOND_JACOBI
                            (not GMRES), the reading of the paper's unnamed "P": BiCGSTAB / TFQMR
                            run on A D^-1 (D = diag(A), right Jacobi) and return x = D^-1 y; COCG
@@ -113,6 +120,9 @@ typedef struct {
                            iterate returned at the step cap. Mixed: ends the inner solve (the
                            next refinement step restarts from the current iterate) */
   int32_t pad_;
+  double robin_lo[2];   /* HELM_PRECOND_ORAS2: dimensionless complex coefficient (re, im) of the
+                           low faces; finite */
+  double robin_hi[2];   /* HELM_PRECOND_ORAS2: the same for the high faces */
 } helm_solve_opts;
 
 typedef struct {

@@ -23,6 +23,15 @@ of the coefficient: robin = i k, the matched impedance (beta rho c = 1) of the w
 + i k rho c B(beta) of the operator, i.e. the first-order absorbing (Despres) condition, the same
 on both sides of an interface.
 
+Two-sided variant (``robin=(c_lo, c_hi)``; the paper's optimized Schwarz method uses two-sided
+interface conditions, i.e. different conditions on the two sides of an interface, and again gives
+no parameters): A_s = R_s A R_s^T + sum over the artificial faces of the extended box of
+(c / h_a) M_face, c = c_lo on the box's low faces (the plane i = i0, j = j0 or l = l0) and c = c_hi
+on its high faces, h_a the lattice spacing normal to the face (a plane that is both, in a box one
+layer thick, takes c_lo). Across an interface the subdomain below sees c_hi and the one above c_lo.
+The coefficients are dimensionless; the reading of their values (a discrete optimisation of the
+pair on a small cabin) is stated where they are used.
+
 Pinned (tests/test_oracle_ras.py): a 1x1x1 partition is the exact inverse (GMRES converges
 in one step); with any partition the preconditioned solution equals the direct solution; the
 interface mass of a box equals the scatter of fem.quad_mass over the box's interface quads.
@@ -61,17 +70,23 @@ def _box_ids(mesh, box):
     return np.sort(ids.ravel())
 
 
-def interface_mass(mesh, ext):
+def interface_mass(mesh, ext, side="both", scaled=False):
     """Face mass (n x n real CSR) of the faces of box ``ext`` that lie inside the lattice: the
-    scatter of fem.quad_mass over every quad of those faces."""
+    scatter of fem.quad_mass over every quad of those faces. side: "both", "lo" (the planes
+    i0, j0, l0) or "hi" (the planes i1-1, j1-1, l1-1, except one that is also a low plane).
+    scaled: each face's mass divided by the lattice spacing normal to it."""
     dims = (mesh.nx + 1, mesh.ny + 1, mesh.nz + 1)
     h = (mesh.Lx / mesh.nx, mesh.Ly / mesh.ny, mesh.Lz / mesh.nz)
     rows, cols, vals = [], [], []
     for a in range(3):
         (lo, hi) = ext[a]
-        planes = [p for p, inside in ((lo, lo > 0), (hi - 1, hi < dims[a])) if inside]
+        planes = []
+        if side in ("both", "lo") and lo > 0:
+            planes.append(lo)
+        if side in ("both", "hi") and hi < dims[a] and not (side == "hi" and lo > 0 and hi - 1 == lo):
+            planes.append(hi - 1)
         u, v = [b for b in range(3) if b != a]
-        Bq = fem.quad_mass(h[u], h[v])
+        Bq = fem.quad_mass(h[u], h[v]) / (h[a] if scaled else 1.0)
         for pa in sorted(set(planes)):
             for cu in range(ext[u][0], ext[u][1] - 1):
                 for cv in range(ext[v][0], ext[v][1] - 1):
@@ -103,7 +118,11 @@ class RAS:
             As = A[E][:, E]
             if robin is not None:
                 F = sp.diags(free[E].astype(np.float64))
-                As = As + robin * (F @ interface_mass(mesh, ext)[E][:, E] @ F)
+                if np.ndim(robin) == 0:
+                    As = As + robin * (F @ interface_mass(mesh, ext)[E][:, E] @ F)
+                else:  # two-sided: dimensionless (c_lo, c_hi), per face times 1 / h_normal
+                    for c, side in zip(robin, ("lo", "hi")):
+                        As = As + c * (F @ interface_mass(mesh, ext, side, scaled=True)[E][:, E] @ F)
             lu = spl.splu(As.tocsc())
             self.blocks.append((E, O, keep, lu))
 

@@ -54,13 +54,16 @@ bool valid_opts(const helm_solve_opts* o) {
   if (!(o->tol > 0.0) || o->maxit < 1) return false;
   if (o->solver == HELM_SOLVER_GMRES && (o->restart < 1 || o->restart > 128)) return false;
   if (o->precond != HELM_PRECOND_NONE && o->precond != HELM_PRECOND_RAS && o->precond != HELM_PRECOND_JACOBI &&
-      o->precond != HELM_PRECOND_ORAS)
+      o->precond != HELM_PRECOND_ORAS && o->precond != HELM_PRECOND_ORAS2)
     return false;
   if (o->precond == HELM_PRECOND_JACOBI && o->solver == HELM_SOLVER_GMRES) return false;
-  if (o->precond == HELM_PRECOND_RAS || o->precond == HELM_PRECOND_ORAS) {
+  if (o->precond == HELM_PRECOND_RAS || o->precond == HELM_PRECOND_ORAS || o->precond == HELM_PRECOND_ORAS2) {
     if (o->solver != HELM_SOLVER_GMRES) return false;
     if (o->ras_parts[0] < 1 || o->ras_parts[1] < 1 || o->ras_parts[2] < 1 || o->ras_overlap < 0) return false;
   }
+  if (o->precond == HELM_PRECOND_ORAS2)
+    for (int q = 0; q < 2; ++q)
+      if (!std::isfinite(o->robin_lo[q]) || !std::isfinite(o->robin_hi[q])) return false;
   if (o->mixed < 0 || o->mixed > 2) return false;
   if (o->mixed) {
     if (o->solver != HELM_SOLVER_COCG) return false;

@@ -405,7 +405,8 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   const size_t nV = (size_t)(m + 1) * n;
   cd* ws = nullptr;
   const size_t ncd = 3 * (size_t)n /*r,w,u*/ + nV + (size_t)(m + 1) * m + 3 * (m + 1) + 2 * m +
-                     (size_t)ntiles * (m + 1) + (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS ? n : 0);
+                     (size_t)ntiles * (m + 1) +
+                     (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS || o.precond == HELM_PRECOND_ORAS2 ? n : 0);
   helm_status stt = dev_alloc(&ws, ncd + 2 * m /*cs*/ + 8);
   if (stt != HELM_OK) return stt;
   GmCtl* dctl = nullptr;
@@ -438,7 +439,10 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   a.y = p; p += m;
   a.part = p; p += (size_t)ntiles * (m + 1);
   a.z = nullptr;
-  if (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS) { a.z = p; p += n; }
+  if (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS || o.precond == HELM_PRECOND_ORAS2) {
+    a.z = p;
+    p += n;
+  }
   a.cs = reinterpret_cast<double*>(p);
   a.ctl = dctl;
   a.tol = o.tol;
@@ -451,11 +455,19 @@ helm_status solve_gmres_system(const helm_ctx* ctx, const int32_t* rowptr, const
   GmCtl* hctl = nullptr;
   cudaError_t e = cudaMallocHost((void**)&hctl, sizeof(GmCtl));
   if (e != cudaSuccess) result = cuda_error(e, "cudaMallocHost");
-  if (result == HELM_OK && (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS)) {
-    // optimized Schwarz: Robin coefficient i k, the matched impedance of the wall term
+  if (result == HELM_OK &&
+      (o.precond == HELM_PRECOND_RAS || o.precond == HELM_PRECOND_ORAS || o.precond == HELM_PRECOND_ORAS2)) {
+    // optimized Schwarz: Robin coefficient i k on every interface face (the matched impedance of
+    // the wall term), or the two-sided pair (robin_lo, robin_hi) / h_normal
     const double k = 2.0 * 3.14159265358979323846 * freq / ctx->phys.c;
-    const cd robin = o.precond == HELM_PRECOND_ORAS ? cd(0.0, k) : cd(0.0, 0.0);
-    result = ras_create(ctx, rowptr, col, val, o.ras_parts, o.ras_overlap, robin, &ras, s);
+    RasRobin rb;
+    if (o.precond == HELM_PRECOND_ORAS) rb.lo = rb.hi = cd(0.0, k);
+    if (o.precond == HELM_PRECOND_ORAS2) {
+      rb.lo = cd(o.robin_lo[0], o.robin_lo[1]);
+      rb.hi = cd(o.robin_hi[0], o.robin_hi[1]);
+      rb.per_h = true;
+    }
+    result = ras_create(ctx, rowptr, col, val, o.ras_parts, o.ras_overlap, rb, &ras, s);
   }
   if (result == HELM_OK) {
     e = cudaMemsetAsync(dctl, 0, sizeof(GmCtl), s);

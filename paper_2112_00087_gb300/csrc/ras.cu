@@ -89,8 +89,10 @@ __global__ void ras_extract(const RasSub* __restrict__ subs, const int32_t* __re
   }
 }
 
-// Optimized-Schwarz interface term: robin * (face mass of the extended box's faces that lie
-// inside the lattice), added to the lower band by columns, Dirichlet rows and columns excluded.
+// Optimized-Schwarz interface terms: c * (face mass of each face of the extended box that lies
+// inside the lattice), c = rb.lo on the box's low faces and rb.hi on its high faces (a plane that
+// is both, in a box one layer thick, takes rb.lo), divided by the spacing normal to the face when
+// rb.per_h; added to the lower band by columns, Dirichlet rows and columns excluded.
 // On a face plane with in-plane axes u, v the Q1 face mass is M1_u (x) M1_v, M1 the 1D linear
 // mass over the face's extent: diagonal h/3 per adjacent interval, neighbours h/6. Thread k owns
 // column k of the band, so no two threads write the same entry.
@@ -101,7 +103,7 @@ __device__ __forceinline__ double mass1d(int c, int dc, int lo, int hi, double h
 }
 
 __global__ void ras_robin(const RasSub* __restrict__ subs, const uint8_t* __restrict__ is_dir, cd* __restrict__ W,
-                          int Nx, int Ny, int Nz, double hx, double hy, double hz, cd robin) {
+                          int Nx, int Ny, int Nz, double hx, double hy, double hz, RasRobin rb) {
   const RasSub S = subs[blockIdx.x];
   cd* Ws = W + S.off;
   const int N[3] = {Nx, Ny, Nz};
@@ -116,6 +118,8 @@ __global__ void ras_robin(const RasSub* __restrict__ subs, const uint8_t* __rest
       const bool on_lo = p[a] == lo[a] && lo[a] > 0;
       const bool on_hi = p[a] == hi_a - 1 && hi_a < N[a];
       if (!on_lo && !on_hi) continue;  // (a one-layer box counts its single plane once)
+      cd robin = on_lo ? rb.lo : rb.hi;
+      if (rb.per_h) robin = cd(robin.re / h[a], robin.im / h[a]);
       const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
       for (int du = -1; du <= 1; ++du)
         for (int dv = -1; dv <= 1; ++dv) {
@@ -264,7 +268,8 @@ std::vector<std::pair<int, int>> block_ranges(int npts, int parts) {
 }  // namespace
 
 helm_status ras_create(const helm_ctx* ctx, const int32_t* rowptr, const int32_t* col, const cd* val,
-                       const int32_t parts[3], int overlap, cd robin, RasPrecond** out, cudaStream_t s) {
+                       const int32_t parts[3], int overlap, const RasRobin& robin, RasPrecond** out,
+                       cudaStream_t s) {
   *out = nullptr;
   const int N[3] = {ctx->mesh.nx + 1, ctx->mesh.ny + 1, ctx->mesh.nz + 1};
   for (int a = 0; a < 3; ++a)
@@ -329,7 +334,7 @@ helm_status ras_create(const helm_ctx* ctx, const int32_t* rowptr, const int32_t
     e = cudaFuncSetAttribute(ras_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) {
     ras_extract<<<P->nsub, 256, 0, s>>>(P->d_sub, rowptr, col, val, P->colband, P->Nx, P->Ny);
-    if (robin.re != 0.0 || robin.im != 0.0)
+    if (robin.lo.re != 0.0 || robin.lo.im != 0.0 || robin.hi.re != 0.0 || robin.hi.im != 0.0)
       ras_robin<<<P->nsub, 256, 0, s>>>(P->d_sub, ctx->is_dir, P->colband, N[0], N[1], N[2],
                                         ctx->mesh.Lx / ctx->mesh.nx, ctx->mesh.Ly / ctx->mesh.ny,
                                         ctx->mesh.Lz / ctx->mesh.nz, robin);

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "NOT_CONV
 HELM_C128, HELM_C64 = 0, 1
 HELM_FMT_CSR, HELM_FMT_DIA27 = 0, 1
 HELM_SOLVER_GMRES, HELM_SOLVER_COCG, HELM_SOLVER_BICGSTAB, HELM_SOLVER_TFQMR = 0, 1, 2, 3
-HELM_PRECOND_NONE, HELM_PRECOND_RAS, HELM_PRECOND_JACOBI, HELM_PRECOND_ORAS = 0, 1, 2, 3
+HELM_PRECOND_NONE, HELM_PRECOND_RAS, HELM_PRECOND_JACOBI, HELM_PRECOND_ORAS, HELM_PRECOND_ORAS2 = 0, 1, 2, 3, 4
 
 # Symbols declared in include/helm.h (tests check the library exports all of them).
 EXPORTED = ["helm_last_error", "helm_create", "helm_destroy", "helm_set_boundary", "helm_sizes",
@@ -53,7 +53,7 @@ class SolveOpts(ctypes.Structure):
                 ("maxit", ctypes.c_int32), ("precond", ctypes.c_int32), ("ras_parts", ctypes.c_int32 * 3),
                 ("ras_overlap", ctypes.c_int32), ("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("inner_maxit", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("stall_window", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("pad_", ctypes.c_int32), ("robin_lo", ctypes.c_double * 2), ("robin_hi", ctypes.c_double * 2)]
 
 
 class Profile(ctypes.Structure):
@@ -137,7 +137,8 @@ def _stream(stream=None):
 
 
 def make_opts(solver="cocg", restart=50, tol=1e-10, maxit=100000, precond=None, ras_parts=(8, 4, 4),
-              ras_overlap=2, mixed=False, inner_tol=1e-4, inner_maxit=5000, max_outer=50, stall_window=0) -> SolveOpts:
+              ras_overlap=2, mixed=False, inner_tol=1e-4, inner_maxit=5000, max_outer=50, stall_window=0,
+              robin=None) -> SolveOpts:
     o = SolveOpts()
     o.solver = {"gmres": HELM_SOLVER_GMRES, "cocg": HELM_SOLVER_COCG, "bicgstab": HELM_SOLVER_BICGSTAB,
                 "tfqmr": HELM_SOLVER_TFQMR}[solver]
@@ -145,7 +146,12 @@ def make_opts(solver="cocg", restart=50, tol=1e-10, maxit=100000, precond=None, 
     o.tol = tol
     o.maxit = maxit
     o.precond = {None: HELM_PRECOND_NONE, "ras": HELM_PRECOND_RAS, "jacobi": HELM_PRECOND_JACOBI,
-                 "oras": HELM_PRECOND_ORAS}[precond]
+                 "oras": HELM_PRECOND_ORAS, "oras2": HELM_PRECOND_ORAS2}[precond]
+    # precond "oras2": robin = (c_lo, c_hi), the dimensionless two-sided interface coefficients
+    if robin is not None:
+        lo, hi = complex(robin[0]), complex(robin[1])
+        o.robin_lo[:] = [lo.real, lo.imag]
+        o.robin_hi[:] = [hi.real, hi.imag]
     o.ras_parts[:] = list(ras_parts)
     o.ras_overlap = ras_overlap
     # mixed: False / True (complex64 inner) / "c64" / "dw" (double-word inner)

@@ -50,3 +50,32 @@ def test_argument_errors_need_no_gpu():
     assert b"nx" in helm.LIB.helm_last_error()
     out = (ctypes.c_double * 2)()
     assert helm.LIB.helm_reduce(7, 10, None, None, out, None) == helm.HELM_ERR_ARG
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of the ABI structs have the C sizes and field offsets (plain C, gcc)
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2112_00087_gb300 import helm
+    structs = {"helm_solve_opts": helm.SolveOpts, "helm_solve_stats": helm.SolveStats,
+               "helm_mesh_desc": helm.MeshDesc, "helm_phys": helm.Phys}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "helm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -5,19 +5,21 @@ from paper_2112_00087_gb300 import autotune as at
 
 
 def fake_solve():
-    # separable cost with its minimum at 3 blocks/SM, 2,048-row tiles, prefetch 0, 4 chunks
+    # separable cost with its minimum at 3 blocks/SM, 2,048-row tiles, 2 tiles per block,
+    # prefetch 0, 4 chunks
     b = int(os.environ["HELM_PERSIST_BLOCKS_PER_SM"])
     t = int(os.environ["HELM_TILE_ROWS"])
+    g = int(os.environ["HELM_TILES_PER_BLOCK"])
     p = int(os.environ["HELM_PREFETCH"])
     c = int(os.environ["HELM_PF_CHUNKS"])
-    return 1.0 + 0.3 * abs(b - 3) + 0.1 * abs(t - 2048) / 2048 + 0.05 * p + 0.02 * abs(c - 4)
+    return 1.0 + 0.3 * abs(b - 3) + 0.1 * abs(t - 2048) / 2048 + 0.04 * abs(g - 2) + 0.05 * p + 0.02 * abs(c - 4)
 
 
 def test_coordinate_descent_finds_the_minimum_and_restores_the_environment():
     before = {k: os.environ.get(k) for k in at.SPACE}
     best, log = at.autotune(fake_solve)
-    assert best == {"HELM_PERSIST_BLOCKS_PER_SM": 3, "HELM_TILE_ROWS": 2048, "HELM_PREFETCH": 0,
-                    "HELM_PF_CHUNKS": 4}
+    assert best == {"HELM_PERSIST_BLOCKS_PER_SM": 3, "HELM_TILE_ROWS": 2048, "HELM_TILES_PER_BLOCK": 2,
+                    "HELM_PREFETCH": 0, "HELM_PF_CHUNKS": 4}
     assert {k: os.environ.get(k) for k in at.SPACE} == before
     keys = [tuple(sorted(c.items())) for c, _ in log]
     assert len(keys) == len(set(keys))  # every setting timed once

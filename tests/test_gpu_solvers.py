@@ -185,6 +185,44 @@ def test_gmres_optimized_schwarz_matches_oracle(dims, parts, overlap, f):
         assert st[0]["iterations"] == 1
 
 
+# the two-sided pair of the discrete optimisation on the 25 x 14 x 12 cabin (times 1 / h)
+TWO_SIDED = (np.exp(0.75j * np.pi), np.exp(-0.75j * np.pi))
+
+
+@pytest.mark.parametrize("dims,parts,overlap,f", [((25, 14, 12), (4, 2, 2), 0, 100.0), ((25, 14, 12), (4, 2, 2), 2, 100.0),
+                                                  ((12, 10, 8), (3, 2, 2), 1, 200.0), ((6, 5, 4), (1, 1, 1), 2, 150.0)])
+def test_gmres_two_sided_optimized_schwarz_matches_oracle(dims, parts, overlap, f):
+    # two-sided interface terms (c_lo / h) M_face on the low faces and (c_hi / h) M_face on the
+    # high faces of every subdomain (paper Sec. 4: optimized Schwarz with two-sided interface
+    # conditions), against the oracle's construction of the same matrices
+    prob = hi.cabin_problem(*dims) if dims[0] > 20 else hi.small_box_problem(*dims)
+    ctx = context(prob)
+    o = helm.make_opts("gmres", restart=50, tol=1e-10, maxit=5000, precond="oras2", ras_parts=parts,
+                       ras_overlap=overlap, robin=TWO_SIDED)
+    p, st = helm.helm_solve(ctx, [f], o)
+    A, b = fem.system(prob, f)
+    P = ras.RAS(A, prob.mesh, parts=parts, overlap=overlap, robin=TWO_SIDED, dir_nodes=prob.dir_nodes)
+    x, ost = krylov.gmres(lambda v: A @ v, b, 50, tol=1e-10, maxit=5000, precond=P)
+    g = p[0].cpu().numpy()
+    assert st[0]["status"] == 0 and ost.converged
+    assert within5(st[0]["iterations"], ost.iterations), (st[0], ost.iterations)
+    assert rel(g, x) <= 1e-9
+    if parts == (1, 1, 1):
+        assert st[0]["iterations"] == 1
+
+
+def test_two_sided_options_are_checked():
+    prob = hi.small_box_problem(6, 5, 4)
+    ctx = context(prob)
+    for bad in ((float("nan"), 1.0), (1.0, float("inf"))):
+        o = helm.make_opts("gmres", restart=20, precond="oras2", ras_parts=(2, 1, 1), robin=bad)
+        with pytest.raises(Exception):
+            helm.helm_solve(ctx, [100.0], o)
+    o = helm.make_opts("cocg", precond="oras2", robin=TWO_SIDED)  # GMRES only
+    with pytest.raises(Exception):
+        helm.helm_solve(ctx, [100.0], o)
+
+
 @pytest.mark.parametrize("dims,f", [((20, 16, 12), 100.0), ((40, 22, 19), 150.0)])
 def test_mixed_precision_refinement(dims, f):
     prob = hi.small_box_problem(*dims) if dims[0] == 20 else hi.cabin_problem(*dims)

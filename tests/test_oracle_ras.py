@@ -56,3 +56,48 @@ def test_robin_schwarz_single_block_and_convergence():
     P = ras.RAS(A, prob.mesh, (3, 2, 2), 1, robin=1j * k, dir_nodes=prob.dir_nodes)
     x, st = krylov.gmres(lambda v: A @ v, b, 30, 1e-12, maxit=3000, precond=P)
     assert st.converged and np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_two_sided_face_masses_split_the_interface_mass():
+    # low faces + high faces = every interface face; "scaled" divides each face by the spacing
+    # normal to it; a one-layer box counts its single plane once, as a low face
+    mesh = hi.Mesh(6, 5, 4, 1.2, 0.8, 0.9)
+    h = (1.2 / 6, 0.8 / 5, 0.9 / 4)
+    ext = ((2, 7), (0, 4), (1, 5))
+    both = ras.interface_mass(mesh, ext).toarray()
+    lo = ras.interface_mass(mesh, ext, "lo").toarray()
+    hi_ = ras.interface_mass(mesh, ext, "hi").toarray()
+    assert np.abs(both - lo - hi_).max() <= 1e-17
+    # the low faces here are x at i=2 and z at l=1, the high face y at j=3
+    assert abs(lo.sum() - (0.48 * 0.675 + 0.8 * 0.48)) <= 1e-14
+    assert abs(hi_.sum() - 0.8 * 0.675) <= 1e-14
+    slo = ras.interface_mass(mesh, ext, "lo", scaled=True).toarray()
+    assert abs(slo.sum() - (0.48 * 0.675 / h[0] + 0.8 * 0.48 / h[2])) <= 1e-12
+    thin = ((3, 4), (0, 6), (0, 5))  # one x-layer inside the lattice
+    assert abs(ras.interface_mass(mesh, thin, "lo").toarray().sum() - 0.8 * 0.9) <= 1e-14
+    assert ras.interface_mass(mesh, thin, "hi").nnz == 0
+    assert np.abs(ras.interface_mass(mesh, thin).toarray() - ras.interface_mass(mesh, thin, "lo").toarray()).max() == 0
+
+
+def test_two_sided_robin_schwarz():
+    prob = hi.small_box_problem(10, 8, 6)  # isotropic lattice: h = 0.1 on every axis
+    m = prob.mesh
+    h = m.Lx / m.nx
+    assert abs(m.Ly / m.ny - h) < 1e-15 and abs(m.Lz / m.nz - h) < 1e-15
+    f = 180.0
+    A, b = fem.system(prob, f)
+    ref = np.linalg.solve(A.toarray(), b)
+    r = np.random.default_rng(5).standard_normal(A.shape[0]) + 0j
+    c = np.exp(0.75j * np.pi)
+    # equal coefficients on both sides: the one-sided preconditioner with robin = c / h
+    P2 = ras.RAS(A, m, (3, 2, 2), 1, robin=(c, c), dir_nodes=prob.dir_nodes)
+    P1 = ras.RAS(A, m, (3, 2, 2), 1, robin=c / h, dir_nodes=prob.dir_nodes)
+    assert np.linalg.norm(P2(r) - P1(r)) <= 1e-12 * np.linalg.norm(P1(r))
+    # different sides: a different preconditioner, still exact for one block, still converging
+    Pc = ras.RAS(A, m, (3, 2, 2), 1, robin=(c, np.conj(c)), dir_nodes=prob.dir_nodes)
+    assert np.linalg.norm(Pc(r) - P1(r)) > 1e-6 * np.linalg.norm(P1(r))
+    Pone = ras.RAS(A, m, (1, 1, 1), 2, robin=(c, np.conj(c)), dir_nodes=prob.dir_nodes)
+    x, st = krylov.gmres(lambda v: A @ v, b, 30, 1e-12, precond=Pone)
+    assert st.iterations == 1 and np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+    x, st = krylov.gmres(lambda v: A @ v, b, 30, 1e-12, maxit=3000, precond=Pc)
+    assert st.converged and np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
