@@ -3,8 +3,9 @@
 The persistent engine reads five launch-shape knobs from the environment at every solve:
 ``HELM_PERSIST_BLOCKS_PER_SM`` (resident blocks per SM, i.e. the register budget),
 ``HELM_TILE_ROWS`` (minimum rows per tile, i.e. how many per-tile reductions a phase pays),
-``HELM_TILES_PER_BLOCK`` (about how many tiles per resident block a system larger than
-tile rows x blocks is cut into, i.e. how finely the dynamic scheduler can balance its tiles),
+``HELM_TILES_PER_BLOCK`` (about how many tiles per resident block a system with more than 4,096
+rows per block is cut into, never below 4,096 rows, i.e. how finely the dynamic scheduler can
+balance its tiles),
 ``HELM_PREFETCH`` (how many block rows ahead each thread of the double-word SpMV prefetches its
 matrix parts into L2) and ``HELM_PF_CHUNKS`` (how many 256-row chunks ahead one thread per
 block bulk-prefetches the vectors of the double-word update phases into L2). ``autotune``
@@ -23,7 +24,7 @@ from __future__ import annotations
 import os
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
-DEFAULTS: Dict[str, int] = {"HELM_PERSIST_BLOCKS_PER_SM": 2, "HELM_TILE_ROWS": 4096, "HELM_TILES_PER_BLOCK": 1,
+DEFAULTS: Dict[str, int] = {"HELM_PERSIST_BLOCKS_PER_SM": 2, "HELM_TILE_ROWS": 4096, "HELM_TILES_PER_BLOCK": 2,
                             "HELM_PREFETCH": 1, "HELM_PF_CHUNKS": 2}
 SPACE: Dict[str, Sequence[int]] = {
     "HELM_PERSIST_BLOCKS_PER_SM": (1, 2, 3),
