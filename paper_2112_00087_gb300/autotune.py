@@ -15,7 +15,8 @@ function that runs one solve under the current environment and returns its time 
 which ``apply`` installs for later solves of the process.
 
 The search is plain coordinate descent from the library defaults: each knob in turn is set to
-each of its candidate values with the others held, the best value is kept, and passes repeat
+each of its candidate values with the others held, the best value is kept (a new value only when
+it is more than 0.5 % faster), and passes repeat
 until a pass changes nothing (or ``max_passes``). Every candidate is timed ``reps`` times and
 scored by its minimum.
 """
@@ -65,11 +66,13 @@ def _timed(run: Callable[[], float], config: Dict[str, int], reps: int) -> float
 
 
 def autotune(run: Callable[[], float], space: Optional[Dict[str, Sequence[int]]] = None,
-             start: Optional[Dict[str, int]] = None, reps: int = 1,
-             max_passes: int = 3) -> Tuple[Dict[str, int], List[Tuple[Dict[str, int], float]]]:
+             start: Optional[Dict[str, int]] = None, reps: int = 1, max_passes: int = 3,
+             min_gain: float = 0.005) -> Tuple[Dict[str, int], List[Tuple[Dict[str, int], float]]]:
     """Coordinate-descent search over `space` (default SPACE) from `start` (default DEFAULTS).
 
     run() executes one solve under the current environment and returns its time in seconds.
+    A candidate replaces the current best only when it is faster by more than the fraction
+    `min_gain` (timing noise, or a knob that does not change the workload, moves nothing).
     Returns (best setting, [(setting, time) for every setting timed, in order]). The process
     environment is left as it was; call apply(best) to use the result."""
     space = dict(SPACE if space is None else space)
@@ -96,7 +99,7 @@ def autotune(run: Callable[[], float], space: Optional[Dict[str, Sequence[int]]]
                 cand = dict(best)
                 cand[knob] = v
                 t = score(cand)
-                if t < best_t:
+                if t < best_t * (1.0 - min_gain):
                     best, best_t, changed = cand, t, True
         if not changed:
             break

@@ -49,3 +49,17 @@ def test_repetitions_take_the_minimum():
 
     best, log = at.autotune(noisy, space={"HELM_PREFETCH": (0, 1)}, start={"HELM_PREFETCH": 1}, reps=2)
     assert all(t == 1.0 for _, t in log) and len(calls) == 4
+
+
+def test_gains_below_the_threshold_keep_the_current_value():
+    # a knob that changes nothing (times equal to 0.03 %) is left at its start value
+    times = {1: 6.7760, 2: 6.7779, 4: 6.7781}
+
+    def run():
+        return times[int(os.environ["HELM_TILES_PER_BLOCK"])]
+
+    best, _ = at.autotune(run, space={"HELM_TILES_PER_BLOCK": (1, 2, 4)}, start={"HELM_TILES_PER_BLOCK": 2})
+    assert best == {"HELM_TILES_PER_BLOCK": 2}
+    best, _ = at.autotune(run, space={"HELM_TILES_PER_BLOCK": (1, 2, 4)}, start={"HELM_TILES_PER_BLOCK": 2},
+                          min_gain=0.0)
+    assert best == {"HELM_TILES_PER_BLOCK": 1}
