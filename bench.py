@@ -43,8 +43,8 @@ TOL = 1e-10
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent launch of the
 # default benchmark step, from a single-pass ncu capture of the full-size run, valid only for
 # the kernel sources it was taken on: reported as null once they change.
-TRAFFIC_CAPTURE = {"config": "sweep256/cocg/dw/jacobi", "sources_sha256_16": "70fb55ad9740cec7",
-                   "bytes": 27004509570816 + 4990162803456}
+TRAFFIC_CAPTURE = {"config": "sweep256/cocg/dw/jacobi", "sources_sha256_16": "62572e8e3aaceb6c",
+                   "bytes": 25750236950016 + 4990120506624}
 KERNEL_SOURCES = ("paper_2112_00087_gb300/csrc/krylov_cocg.cu", "paper_2112_00087_gb300/csrc/krylov_engine.cuh",
                   "paper_2112_00087_gb300/csrc/kernels.cuh", "paper_2112_00087_gb300/csrc/dw.cuh",
                   "paper_2112_00087_gb300/csrc/common.cuh", "paper_2112_00087_gb300/csrc/krylov_host.cu",
@@ -113,14 +113,18 @@ def bicgstab_bytes(n, nnz, st):
 
 
 def cocg_dw_bytes(n, nnz, st):
-    """Double-word mixed mode: inner steps move what an FP64 step moves (matrix parts as 8-byte
-    (hi, lo) float pairs, vectors as 16-byte complex double-words), plus the FP64 refinement
-    residuals, inner starts (r read, r and d written) and corrections (d and x read, x written)."""
+    """Double-word mixed mode: an inner step moves the SpMV (matrix parts as 8-byte (hi, lo) float
+    pairs, x read once and y written once as 16-byte complex double-words), the r update (q and r
+    read, r written: 48n) and the x and p updates together (r, p, x read, p and x written: 80n), 376
+    bytes per row; FP64 fallback steps move an FP64 step's bytes; plus the FP64 refinement
+    residuals, inner starts (r read, r and d written) and corrections (d, p and x read, x
+    written)."""
     it_in, outer = st["iterations_c64"], abs(st["outer"])
     it64 = st["iterations"] - it_in
-    step = dia_spmv_bytes(n, 16) + 96 * n + 48 * n
+    step = dia_spmv_bytes(n, 16) + 48 * n + 80 * n
+    step64 = dia_spmv_bytes(n, 16) + 96 * n + 48 * n
     resid = dia_spmv_bytes(n, 16) + 32 * n
-    return it_in * step + it64 * step + (outer + 1) * resid + outer * (48 * n + 48 * n) + 48 * n
+    return it_in * step + it64 * step64 + (outer + 1) * resid + outer * (48 * n + 64 * n) + 48 * n
 
 
 def tfqmr_bytes(n, nnz, st):

@@ -722,14 +722,14 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
     }
     return;
   }
+  // r -= alpha q here; x += alpha p is left to phase C, which reads p anyway (same values)
   const cd al = S->alpha;
-  const cws a = to_cws(al.re, al.im);
   const cws ma = to_cws(-al.re, -al.im);
   dacc2 rr;
   float nrm = 0.f;  // ||r||^2 for the stopping estimate (FP32 is enough for a threshold test)
-  // thread 0 keeps the block's next `pf_chunks` row chunks of p, q, x, r on their way into L2
+  // thread 0 keeps the block's next `pf_chunks` row chunks of q, r on their way into L2
   const int d = P.pf_chunks;
-  const cw* const vecs[4] = {Y.pw, Y.qw, Y.xw, Y.rw};
+  const cw* const vecs[2] = {Y.qw, Y.rw};
   if (threadIdx.x == 0)
     for (int j = 0; j < d; ++j) prefetch_rows(vecs, T.row0 + (int64_t)j * kBlock, T.row1);
   // HELM_VEC_UNROLL rows per thread per pass, all of their loads issued before the arithmetic
@@ -738,15 +738,13 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
     if (threadIdx.x == 0 && d > 0)
 #pragma unroll
       for (int u = 0; u < U; ++u) prefetch_rows(vecs, i0 + (int64_t)(d + u) * kBlock, T.row1);
-    cw pv[U], qv[U], xv[U], rv[U];
+    cw qv[U], rv[U];
     float wv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
       if (i < T.row1) {
-        pv[u] = Y.pw[i];
         qv[u] = Y.qw[i];
-        xv[u] = Y.xw[i];
         rv[u] = Y.rw[i];
         wv[u] = wnorm32(Y, i);
       }
@@ -755,9 +753,7 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
     for (int u = 0; u < U; ++u) {
       const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
       if (i < T.row1) {
-        const cw xn = cw_axpy2(xv[u], a, pv[u]);
         const cw rn = cw_axpy2(rv[u], ma, qv[u]);
-        Y.xw[i] = xn;
         Y.rw[i] = rn;
         cw_dotu_acc2(rr, rn, rn);
         nrm = fmaf(wv[u], fmaf(rn.rh, rn.rh, rn.ih * rn.ih), nrm);
@@ -801,11 +797,15 @@ __device__ void phaseC_dw(const KParams& P, int t, double* sh) {
     resid_phaseC(P, S, Y);
     return;
   }
+  // the step's x += alpha p (deferred from phase B), then p = r + beta p -- or, when the inner
+  // solve ends, the refinement update with the finished correction
+  const cd al = S->alpha;
+  const cws a = to_cws(al.re, al.im);
   if (vload(&S->cmode) == C_PUPDATE) {
     const cd be = S->beta;
     const cws b = to_cws(be.re, be.im);
     const int d = P.pf_chunks;
-    const cw* const vecs[2] = {Y.rw, Y.pw};
+    const cw* const vecs[3] = {Y.rw, Y.pw, Y.xw};
     if (threadIdx.x == 0)
       for (int j = 0; j < d; ++j) prefetch_rows(vecs, T.row0 + (int64_t)j * kBlock, T.row1);
     constexpr int U = HELM_VEC_UNROLL;
@@ -813,27 +813,31 @@ __device__ void phaseC_dw(const KParams& P, int t, double* sh) {
       if (threadIdx.x == 0 && d > 0)
 #pragma unroll
         for (int u = 0; u < U; ++u) prefetch_rows(vecs, i0 + (int64_t)(d + u) * kBlock, T.row1);
-      cw rv[U], pv[U];
+      cw rv[U], pv[U], xv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
         if (i < T.row1) {
           rv[u] = Y.rw[i];
           pv[u] = Y.pw[i];
+          xv[u] = Y.xw[i];
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t i = i0 + (int64_t)u * kBlock + threadIdx.x;
-        if (i < T.row1) Y.pw[i] = cw_axpy2(rv[u], b, pv[u]);
+        if (i < T.row1) {
+          Y.xw[i] = cw_axpy2(xv[u], a, pv[u]);
+          Y.pw[i] = cw_axpy2(rv[u], b, pv[u]);
+        }
       }
     }
     return;
   }
-  // refinement update x += ||r|| d (FP64)
+  // refinement update x += ||r|| d (FP64), d the inner solution after its last step
   const double sc = vload(&S->discard) ? 0.0 : S->rnorm;
   for (int64_t i = T.row0 + threadIdx.x; i < T.row1; i += kBlock) {
-    const cw d = Y.xw[i];
+    const cw d = cw_axpy2(Y.xw[i], a, Y.pw[i]);
     cd xi = Y.x[i];
     xi.re = fma(sc, join_double(d.rh, d.rl), xi.re);
     xi.im = fma(sc, join_double(d.ih, d.il), xi.im);
