@@ -732,8 +732,10 @@ __device__ void phaseB_dw(const KParams& P, int t, double* sh) {
   const cw* const vecs[2] = {Y.qw, Y.rw};
   if (threadIdx.x == 0)
     for (int j = 0; j < d; ++j) prefetch_rows(vecs, T.row0 + (int64_t)j * kBlock, T.row1);
-  // HELM_VEC_UNROLL rows per thread per pass, all of their loads issued before the arithmetic
-  constexpr int U = HELM_VEC_UNROLL;
+  // four rows per thread per pass, all of their loads issued before the arithmetic (the phase
+  // streams only q and r, so the rows' loads fit in registers; the rows are still taken, and
+  // their dot-product terms added, in the same order as one row per pass)
+  constexpr int U = 4;
   for (int64_t i0 = T.row0; i0 < T.row1; i0 += U * kBlock) {
     if (threadIdx.x == 0 && d > 0)
 #pragma unroll
