@@ -42,6 +42,10 @@ by step in complex128 numpy, the two iterations the GPU path runs:
   (z = D^-1 r, rho = r^T z, p = z + beta p); in exact arithmetic its iterates equal those of COCG
   on S A S (S = D^-1/2) mapped back by x = S y, the form ``sym_jacobi`` builds -- an independent
   formulation used to cross-check that one.
+* ``cocg_inner_qrec``: the inner COCG of the refinement with the product taken of the residual
+  (w = A s) and A p carried by the recurrence q = w + beta q -- the same iteration in exact
+  arithmetic, in the form where a parallel step needs one synchronisation point fewer; used to
+  measure how far that form moves the step counts (oracle/measure_qrec.py).
 * ``right_jacobi``: the "P" of the paper's P-BiCGSTAB / P-TFQMR read as Jacobi, applied on the
   right (A D^-1 y = b, x = D^-1 y, D = diag(A)), so residuals stay those of A x = b.
 
@@ -443,6 +447,39 @@ def cocg_inner(matvec, s, target, inner_maxit, maxit_left, stall, nrm):
             return d, k, est, False, hist
         rho_new = dotu(s, s)
         p = s + (rho_new / rho) * p
+        rho = rho_new
+
+
+def cocg_inner_qrec(matvec, s, target, inner_maxit, maxit_left, stall, nrm):
+    """``cocg_inner`` with the product taken of the residual: each step forms w = A s and gets
+    A p from the recurrence q = w + beta q alongside p = s + beta p, so q = A p in exact
+    arithmetic and drifts from it by rounding in floating point. In this form one pass over the
+    rows can take the product and update both directions, i.e. a parallel step needs one global
+    synchronisation point fewer. Same stopping rules and results as ``cocg_inner``."""
+    d = np.zeros_like(s)
+    p = s.copy()
+    q = matvec(p)
+    rho = dotu(s, s)
+    best, best_it, k, est, hist = 1.0, 0, 0, 1.0, []
+    while True:
+        k += 1
+        mu = dotu(p, q)
+        if mu == 0 or rho == 0:
+            return d, k, est, True, hist
+        alpha = rho / mu
+        d = d + alpha * p
+        s = s - alpha * q
+        est = nrm(s)
+        hist.append(est)
+        if est < 0.5 * best:
+            best, best_it = est, k
+        if est <= target or k >= inner_maxit or k >= maxit_left or (stall and k - best_it >= stall):
+            return d, k, est, False, hist
+        rho_new = dotu(s, s)
+        beta = rho_new / rho
+        w = matvec(s)
+        p = s + beta * p
+        q = w + beta * q
         rho = rho_new
 
 

@@ -332,3 +332,38 @@ def test_gmres_inner_complex64_stops_at_its_target():
     d, k, est, bd, hist = krylov.gmres_inner_c64(lambda v: A32 @ v, s, 40, 1e-4, 10000)
     assert est <= 1e-4 and not bd
     assert np.linalg.norm(s - A @ d) <= 2e-4  # the FP64 residual of the correction, to complex64 accuracy
+
+
+def test_residual_product_form_of_the_inner_cocg():
+    # cocg_inner_qrec is cocg_inner with A p carried by a recurrence: the same iteration in
+    # exact arithmetic, so the first residual estimates agree to rounding (a wrong recurrence --
+    # q = w + beta p, p = s + beta q, a missing beta -- breaks this at the second step), and
+    # through the refinement it reaches the dense-LU solution
+    for dims, f in (((10, 8, 6), 100.0), ((13, 7, 5), 230.0)):
+        prob = hi.small_box_problem(*dims)
+        A, b = fem.system(prob, f)
+        Ah, s, w = krylov.sym_jacobi(A)
+        mv = lambda v: Ah @ v  # noqa: E731
+        rhs = s * b / np.linalg.norm(s * b)
+        nrm = krylov.nrm2
+        _, k1, _, _, h1 = krylov.cocg_inner(mv, rhs, 1e-12, 5000, 5000, None, nrm)
+        _, k2, _, _, h2 = krylov.cocg_inner_qrec(mv, rhs, 1e-12, 5000, 5000, None, nrm)
+        assert np.allclose(h1[:12], h2[:12], rtol=1e-8, atol=0)
+        assert abs(k1 - k2) <= max(3, 0.1 * k1), (k1, k2)
+        ref = np.linalg.solve(A.toarray(), b)
+        y, st, outer = krylov.cocg_ir(mv, s * b, tol=1e-12, weights=w,
+                                      inner=lambda s_, t_, im_, ml_, st_, nm_: krylov.cocg_inner_qrec(
+                                          mv, s_, t_, im_, ml_, st_, nm_))
+        assert st.converged and outer >= 1
+        assert np.linalg.norm(s * y - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_residual_product_form_is_cg_on_spd():
+    # real SPD (1D Laplacian): the recurrence form is CG, n steps in exact arithmetic
+    n = 40
+    A = sp.diags([-np.ones(n - 1), 2.0 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    b = np.random.default_rng(7).standard_normal(n) + 0j
+    d, k, est, bd, _ = krylov.cocg_inner_qrec(lambda v: A @ v, b / np.linalg.norm(b), 1e-12, 200, 200, None,
+                                             krylov.nrm2)
+    assert not bd and est <= 1e-12 and k <= n + 2
+    assert np.linalg.norm(A @ d - b / np.linalg.norm(b)) <= 1e-10
