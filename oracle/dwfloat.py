@@ -231,10 +231,12 @@ def dotu(x, y):
     return complex(math.fsum(p.real), math.fsum(p.imag))
 
 
-def make_inner(M):
+def make_inner(M, form="plain"):
     """An inner solve for krylov.cocg_ir: COCG on M d = s in double-word arithmetic (M a
     StencilMatrix), the same steps and stopping rule as krylov.cocg_inner; scalars (alpha, beta)
-    in float64, rounded to double-word where they scale a vector."""
+    in float64, rounded to double-word where they scale a vector. form="qrec": the steps of
+    krylov.cocg_inner_qrec instead (the product taken of the residual, w = M r, and M p carried
+    by q = w + beta q)."""
 
     def inner(s, target, inner_maxit, maxit_left, stall, nrm):
         r = CW.from_complex(s)
@@ -242,8 +244,11 @@ def make_inner(M):
         p = r.copy()
         rho = dotu(r, r)
         best, best_it, k, est, hist = 1.0, 0, 0, 1.0, []
-        while True:
+        if form == "qrec":
             q = M.matvec(p)
+        while True:
+            if form != "qrec":
+                q = M.matvec(p)
             k += 1
             mu = dotu(p, q)
             if mu == 0 or rho == 0:
@@ -258,7 +263,13 @@ def make_inner(M):
             if est <= target or k >= inner_maxit or k >= maxit_left or (stall and k - best_it >= stall):
                 return d.to_complex(), k, est, False, hist
             rho_new = dotu(r, r)
-            p = axpy(r, rho_new / rho, p)
+            if form == "qrec":
+                w = M.matvec(r)
+                beta = rho_new / rho
+                p = axpy(r, beta, p)
+                q = axpy(w, beta, q)
+            else:
+                p = axpy(r, rho_new / rho, p)
             rho = rho_new
 
     return inner

@@ -8,7 +8,10 @@ For each system, on the symmetric-Jacobi scaled system, FP64 throughout, target 
 sides perturbed at the rounding level (1e-14 of the largest entry, seeds 1-3), i.e. each form's
 rounding spread of the step count, and the number of refinement steps each took.
 
-Run from the repository root:  python oracle/measure_qrec.py [sweep indices ...]
+With --dw both inner solves run in double-word arithmetic (oracle.dwfloat.make_inner, forms
+"plain" and "qrec"), the arithmetic of the GPU's inner solve.
+
+Run from the repository root:  python oracle/measure_qrec.py [--dw] [sweep indices ...]
 """
 import multiprocessing as mp
 import os
@@ -31,16 +34,19 @@ def perturbed(b, seed):
 
 
 def one(args):
-    k, form, seed = args
+    k, form, seed, use_dw = args
     import helm_inputs as hi
-    from oracle import fem, krylov
+    from oracle import dwfloat, fem, krylov
     f = float(hi.sweep_freqs(256)[k])
     prob = hi.cabin_problem(*hi.sweep_mesh_dims(f))
     A, b = fem.system(prob, f)
     Ah, s, w = krylov.sym_jacobi(A)
     mv = lambda v: Ah @ v  # noqa: E731
     inner = None
-    if form == "qrec":
+    if use_dw:
+        m = prob.mesh
+        inner = dwfloat.make_inner(dwfloat.StencilMatrix(dwfloat.slots_from_csr(Ah, m.nx, m.ny), m.nx, m.ny), form=form)
+    elif form == "qrec":
         inner = lambda s_, t_, im_, ml_, st_, nm_: krylov.cocg_inner_qrec(mv, s_, t_, im_, ml_, st_, nm_)  # noqa: E731
     _, st, outer = krylov.cocg_ir(mv, perturbed(s * b, seed), tol=1e-10, inner_maxit=45000, maxit=45000,
                                   stall=15000, weights=w, inner=inner)
@@ -48,8 +54,9 @@ def one(args):
 
 
 def main():
-    ks = [int(a) for a in sys.argv[1:]] or list(range(0, 161, 16)) + [176, 192, 208]
-    work = [(k, form, sd) for k in ks for form in ("plain", "qrec") for sd in SEEDS]
+    use_dw = "--dw" in sys.argv[1:]
+    ks = [int(a) for a in sys.argv[1:] if a != "--dw"] or list(range(0, 161, 16)) + [176, 192, 208]
+    work = [(k, form, sd, use_dw) for k in ks for form in ("plain", "qrec") for sd in SEEDS]
     res = {}
     with mp.get_context("spawn").Pool(os.cpu_count()) as pool:
         for k, form, sd, it, outer, cv, n, f in pool.imap_unordered(one, work):

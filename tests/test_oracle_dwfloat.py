@@ -120,3 +120,23 @@ def test_double_word_inner_solve_through_refinement_matches_dense_lu(dims, f):
     _, st_64, o2 = krylov.cocg_ir(mv, s * b, tol=1e-10, weights=w)
     assert o1 == o2 == 1
     assert abs(st_dw.iterations - st_64.iterations) <= max(2, 0.05 * st_64.iterations)
+
+
+def test_double_word_inner_solve_in_the_residual_product_form():
+    # form="qrec" follows krylov.cocg_inner_qrec in double-word arithmetic: its first residual
+    # estimates agree with the plain double-word inner solve's to the format's rounding, and the
+    # refinement around it reaches the dense-LU solution
+    prob = hi.small_box_problem(10, 8, 6)
+    A, b = fem.system(prob, 150.0)
+    ref = np.linalg.solve(A.toarray(), b)
+    Ah, s, w = krylov.sym_jacobi(A)
+    m = prob.mesh
+    M = dw.StencilMatrix(dw.slots_from_csr(Ah, m.nx, m.ny), m.nx, m.ny)
+    rhs = s * b / np.linalg.norm(s * b)
+    _, k1, _, _, h1 = dw.make_inner(M)(rhs, 1e-12, 5000, 5000, None, krylov.nrm2)
+    _, k2, _, _, h2 = dw.make_inner(M, form="qrec")(rhs, 1e-12, 5000, 5000, None, krylov.nrm2)
+    assert np.allclose(h1[:12], h2[:12], rtol=1e-8, atol=0)
+    assert abs(k1 - k2) <= max(3, 0.1 * k1), (k1, k2)
+    y, st, outer = krylov.cocg_ir(lambda v: Ah @ v, s * b, tol=1e-12, weights=w, inner=dw.make_inner(M, form="qrec"))
+    assert st.converged and outer >= 1
+    assert np.linalg.norm(s * y - ref) <= 1e-9 * np.linalg.norm(ref)
