@@ -8,12 +8,14 @@ mixed-precision GPU solves run):
     right-hand side and for three right-hand sides perturbed at the rounding level (1e-14 of the
     largest entry, seeds 1-3), i.e. the rounding spread of the step count: with the inner solve
     in FP64 ("iterations") and in double-word arithmetic (oracle.dwfloat, "iterations_dw"), the
-    arithmetic of the GPU's inner solve, which decides its step count;
+    arithmetic of the GPU's inner solve, which decides its step count; and in double-word
+    arithmetic in the residual-product form of the inner COCG (dwfloat.make_inner(form="qrec"),
+    "iterations_dw_qrec"), the iteration of a GPU form with one synchronisation point fewer;
   * the solution at relative residual 1e-13 (FP64 inner solve) sampled at 128 seeded node
     indices, its 2-norm and the relative residual reached.
 
 Only oracle/ and the seeded input generators are used. Run from the repository root:
-    python tests/golden/make_sweep_refs.py [--jobs 8] [--kinds value fp64 dw]
+    python tests/golden/make_sweep_refs.py [--jobs 8] [--kinds value fp64 dw dwq] [--systems ...]
 (results of the kinds run are merged into an existing file; the FP64 kinds take about an hour on
 8 cores, the double-word counts about three; the 901,152-node system dominates both).
 """
@@ -76,9 +78,10 @@ def job(args):
                          "im": [float(v) for v in x[idx].imag], "seconds": time.time() - t0}
     kind, seed = what
     inner = None
-    if kind == "dw":
+    if kind in ("dw", "dwq"):
         m = prob.mesh
-        inner = dwfloat.make_inner(dwfloat.StencilMatrix(dwfloat.slots_from_csr(Ah, m.nx, m.ny), m.nx, m.ny))
+        inner = dwfloat.make_inner(dwfloat.StencilMatrix(dwfloat.slots_from_csr(Ah, m.nx, m.ny), m.nx, m.ny),
+                                   form="qrec" if kind == "dwq" else "plain")
     rhs = s * b if seed == 0 else perturbed_rhs(s * b, seed)
     _, st, outer = krylov.cocg_ir(mv, rhs, tol=TOL, inner_maxit=MAXIT, maxit=MAXIT, stall=STALL, weights=w,
                                   inner=inner)
@@ -90,14 +93,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=os.cpu_count())
     ap.add_argument("--systems", type=int, nargs="*", default=list(SYSTEMS))
-    ap.add_argument("--kinds", nargs="*", default=["value", "fp64", "dw"], choices=["value", "fp64", "dw"])
+    ap.add_argument("--kinds", nargs="*", default=["value", "fp64", "dw"], choices=["value", "fp64", "dw", "dwq"])
     args = ap.parse_args()
     import helm_inputs as hi
     path = os.path.join(HERE, "sweep_refs.json")
     out = {"tol": TOL, "value_tol": VALUE_TOL, "stall": STALL, "maxit": MAXIT, "nsample": NSAMPLE,
            "perturb_seeds": list(PERTURB_SEEDS),
            "solver": "oracle.krylov.cocg_ir on the symmetric-Jacobi scaled system; inner solve in FP64 "
-                     "(iterations, value) or in double-word arithmetic, oracle.dwfloat (iterations_dw)",
+                     "(iterations, value) or in double-word arithmetic, oracle.dwfloat (iterations_dw; "
+                     "residual-product form: iterations_dw_qrec)",
            "systems": {}}
     if os.path.exists(path):
         old = json.load(open(path))
@@ -106,7 +110,7 @@ def main():
     for k in sorted(args.systems, reverse=True):
         if "value" in args.kinds:
             work.append((k, "value"))
-        for kind in ("fp64", "dw"):
+        for kind in ("fp64", "dw", "dwq"):
             if kind in args.kinds:
                 work += [(k, (kind, sd)) for sd in (0,) + PERTURB_SEEDS]
     for k in args.systems:
@@ -124,7 +128,7 @@ def main():
             print(k, what, {a: b for a, b in res.items() if a not in ("idx", "re", "im")}, flush=True)
     for (k, kind), c in counts.items():
         rec = out["systems"][str(k)]
-        sfx = "" if kind == "fp64" else "_dw"
+        sfx = {"fp64": "", "dw": "_dw", "dwq": "_dw_qrec"}[kind]
         rec["iterations" + sfx] = [c[sd]["iterations"] for sd in (0,) + PERTURB_SEEDS]
         rec["outer" + sfx] = [c[sd]["outer"] for sd in (0,) + PERTURB_SEEDS]
         rec["converged" + sfx] = all(c[sd]["converged"] for sd in (0,) + PERTURB_SEEDS)
